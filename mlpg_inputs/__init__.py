@@ -1,0 +1,268 @@
+"""Seeded synthetic inputs for the MLPG/RK discrete-ordinates transport solve.
+
+This module is shared by the tests, the benchmark and the CPU oracle.  It holds
+only input generation: point clouds, angular quadrature sets, per-point material
+data.  None of the discretisation arithmetic (kernels, RK corrections, cells,
+quadrature over cells, assembly, solvers) lives here.
+
+Point sets follow the perturbed-lattice recipe of Sec. 5 ("Manufactured
+problems"): a uniform lattice whose coordinates are each displaced by
+gamma * spacing with gamma uniform in [-0.2, 0.2], independently per point and
+dimension.  Lattice points are cell-centred in the unit box.
+
+Angular sets are level-symmetric S_N quadratures built here by even-moment
+matching (the paper's own LDFE sets are only cited, Sec. 4.3).  In 2D the
+directions of the upper hemisphere (Omega_z > 0) are kept with doubled weights,
+so that sum(w) = 4*pi as in the 3D transport equation (Eq. transport-equation,
+Sec. 4.1).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+FOUR_PI = 4.0 * math.pi
+
+
+# --------------------------------------------------------------------------
+# point sets
+# --------------------------------------------------------------------------
+def jittered_lattice(n_per_dim: int, dim: int, seed: int, lo: float = 0.0,
+                     hi: float = 1.0, jitter: float = 0.2):
+    """Cell-centred lattice of n_per_dim**dim points in [lo, hi]^dim.
+
+    Each coordinate is moved by spacing * gamma, gamma ~ U[-jitter, jitter]
+    (numpy PCG64(seed)), as in Sec. 5.  Returns (x[n, dim], spacing).
+    Point order: the last coordinate varies slowest (row-major over (z, y, x)).
+    """
+    h = (hi - lo) / n_per_dim
+    axes = [lo + (np.arange(n_per_dim) + 0.5) * h for _ in range(dim)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]  # x fastest
+    x = np.stack([g.reshape(-1) for g in grids], axis=1).astype(np.float64)
+    if jitter > 0.0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        x = x + h * rng.uniform(-jitter, jitter, size=x.shape)
+    return np.ascontiguousarray(x), h
+
+
+# --------------------------------------------------------------------------
+# level-symmetric angular quadrature by even-moment matching
+# --------------------------------------------------------------------------
+def _octant_points(n_levels: int):
+    """Index triples (a, b, c), 1-based levels with a + b + c = n_levels + 2."""
+    pts = []
+    for a in range(1, n_levels + 1):
+        for b in range(1, n_levels + 1):
+            c = n_levels + 2 - a - b
+            if c >= 1:
+                pts.append((a, b, c))
+    return pts
+
+
+def _ls_weights(order: int, mu1: float):
+    """Per-class weights matching the even moments for a given mu1.
+
+    Returns (mu levels, points, class of each point, class weights) with the
+    octant normalised to 4*pi/8.  Moments used: k = 0 and k = 2..n_classes
+    (k = 1 holds for every symmetric set and adds no equation).
+    """
+    n = order // 2
+    if n == 1:
+        mu = np.array([math.sqrt(1.0 / 3.0)])
+    else:
+        delta = 2.0 * (1.0 - 3.0 * mu1 * mu1) / (order - 2)
+        mu2 = mu1 * mu1 + delta * np.arange(n)
+        if np.any(mu2 <= 0.0):
+            return None
+        mu = np.sqrt(mu2)
+    pts = _octant_points(n)
+    classes = sorted({tuple(sorted(p)) for p in pts})
+    cls_of = [classes.index(tuple(sorted(p))) for p in pts]
+    ncls = len(classes)
+    ks = [0] + list(range(2, ncls + 1))
+    A = np.zeros((ncls, ncls))
+    rhs = np.zeros(ncls)
+    for r, k in enumerate(ks):
+        for p, c in zip(pts, cls_of):
+            A[r, c] += mu[p[0] - 1] ** (2 * k)
+        rhs[r] = FOUR_PI / 8.0 / (2 * k + 1)
+    try:
+        wc = np.linalg.solve(A, rhs)
+    except np.linalg.LinAlgError:
+        return None
+    return mu, pts, cls_of, wc
+
+
+def _next_moment_residual(order: int, mu1: float):
+    got = _ls_weights(order, mu1)
+    if got is None:
+        return None, None
+    mu, pts, cls_of, wc = got
+    k = len(wc) + 1
+    s = sum(wc[c] * mu[p[0] - 1] ** (2 * k) for p, c in zip(pts, cls_of))
+    return s - FOUR_PI / 8.0 / (2 * k + 1), wc
+
+
+def level_symmetric(order: int, dim: int):
+    """Level-symmetric S_N set: (omega[M, 3], w[M]) with sum(w) = 4*pi.
+
+    mu1 is the root, in (0, 1/sqrt(3)), of the first even moment not used for
+    the weights, taken among roots with all class weights positive (the root
+    with the largest mu1 when several exist).  3D: N(N+2) directions; 2D: the
+    N(N+2)/2 directions with Omega_z > 0, weights doubled.
+    """
+    if order < 2 or order % 2:
+        raise ValueError("S_N order must be even and >= 2")
+    n = order // 2
+    if n == 1:
+        mu1 = math.sqrt(1.0 / 3.0)
+    else:
+        grid = np.linspace(1e-4, math.sqrt(1.0 / 3.0) - 1e-6, 4000)
+        roots = []
+        prev = None
+        for g in grid:
+            res, wc = _next_moment_residual(order, g)
+            if res is not None and prev is not None and prev[0] is not None \
+                    and np.sign(res) != np.sign(prev[0]):
+                a, b = prev[1], g
+                fa = prev[0]
+                for _ in range(200):
+                    mid = 0.5 * (a + b)
+                    fm, _ = _next_moment_residual(order, mid)
+                    if fm is None:
+                        break
+                    if np.sign(fm) == np.sign(fa):
+                        a, fa = mid, fm
+                    else:
+                        b = mid
+                r = 0.5 * (a + b)
+                _, wr = _next_moment_residual(order, r)
+                if wr is not None and np.all(wr > 0):
+                    roots.append(r)
+            prev = (res, g)
+        if roots:
+            mu1 = max(roots)
+        else:  # no moment root with positive weights: smallest residual
+            best = None
+            for g in grid:
+                res, wc = _next_moment_residual(order, g)
+                if res is None or not np.all(wc > 0):
+                    continue
+                if best is None or abs(res) < best[0]:
+                    best = (abs(res), g)
+            if best is None:
+                raise ValueError(f"no positive level-symmetric S{order} set")
+            mu1 = best[1]
+    mu, pts, cls_of, wc = _ls_weights(order, mu1)
+    dirs, wts = [], []
+    for sx, sy, sz in itertools.product((1.0, -1.0), repeat=3):
+        if dim == 2 and sz < 0:
+            continue
+        for p, c in zip(pts, cls_of):
+            dirs.append((sx * mu[p[0] - 1], sy * mu[p[1] - 1], sz * mu[p[2] - 1]))
+            wts.append(wc[c] * (2.0 if dim == 2 else 1.0))
+    omega = np.asarray(dirs, dtype=np.float64)
+    w = np.asarray(wts, dtype=np.float64)
+    w *= FOUR_PI / w.sum()
+    return np.ascontiguousarray(omega), np.ascontiguousarray(w)
+
+
+# --------------------------------------------------------------------------
+# problem descriptions
+# --------------------------------------------------------------------------
+@dataclass
+class Problem:
+    """One transport problem: points, extents, angular set, materials, steps."""
+    name: str
+    dim: int
+    x: np.ndarray            # [n, dim]
+    R: np.ndarray            # [n] kernel support radius (2 * spacing)
+    omega: np.ndarray        # [m, 3]
+    w: np.ndarray            # [m]
+    sigma_t: np.ndarray      # [n]
+    sigma_s: np.ndarray      # [n]
+    q: np.ndarray            # [n] isotropic source per steradian
+    dt: float
+    steps: int
+    lo: tuple = (0.0, 0.0, 0.0)
+    hi: tuple = (1.0, 1.0, 1.0)
+    inflow: dict = field(default_factory=dict)   # face -> psi_b
+    spacing: float = 0.0
+
+    @property
+    def n(self):
+        return self.x.shape[0]
+
+    @property
+    def m(self):
+        return self.omega.shape[0]
+
+
+def make_problem(name: str, n_per_dim: int, dim: int, sn: int, seed: int,
+                 sigma_t, sigma_s, q, dt: float, steps: int,
+                 inflow=None, support: float = 2.0, jitter: float = 0.2):
+    """Build a Problem on a jittered unit-box lattice.
+
+    sigma_t / sigma_s / q are scalars or callables f(x[n, dim], rng) -> [n]
+    evaluated at the points (constant over each point's cell).
+    """
+    x, h = jittered_lattice(n_per_dim, dim, seed, jitter=jitter)
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    def ev(v, *extra):
+        if callable(v):
+            return np.ascontiguousarray(np.asarray(v(x, rng, *extra), dtype=np.float64))
+        return np.full(x.shape[0], float(v))
+    st = ev(sigma_t)
+    ss = ev(sigma_s, st) if callable(sigma_s) else np.full(x.shape[0], float(sigma_s))
+    qq = ev(q)
+    omega, w = level_symmetric(sn, dim)
+    return Problem(name=name, dim=dim, x=x, R=np.full(x.shape[0], support * h),
+                   omega=omega, w=w, sigma_t=st, sigma_s=ss, q=qq, dt=dt,
+                   steps=steps, inflow=dict(inflow or {}), spacing=h)
+
+
+def small_2d(n_per_dim: int = 32, sn: int = 4, seed: int = 1000, steps: int = 10,
+             dt: float = 0.01, sigma_t: float = 1.0, sigma_s: float = 0.5,
+             q: float = 1.0, jitter: float = 0.2):
+    """2D unit square, n_per_dim^2 jittered points, support 2h, linear RK,
+    level-symmetric S_sn, uniform sigma_t / sigma_s / q, vacuum boundaries,
+    c = 1, backward Euler.  Defaults: 32x32 points, S4 (12 directions),
+    sigma_t = 1, sigma_s = 0.5, q = 1, dt = 0.01, 10 steps."""
+    return make_problem(f"2d-{n_per_dim}x{n_per_dim}-S{sn}", n_per_dim, 2, sn, seed,
+                        sigma_t, sigma_s, q, dt, steps, jitter=jitter)
+
+
+def two_region_2d(n_per_dim: int = 256, sn: int = 8, seed: int = 2000, steps: int = 20,
+                  dt: float = 0.005, ratio: float = 0.9):
+    """2D unit square, jittered lattice, S_sn, sigma_t = 100 for points in the
+    centred square [0.4, 0.6]^2 and 1 elsewhere, sigma_s = ratio * sigma_t,
+    q = 1 for points with x < 0.5 and 0 elsewhere, vacuum boundaries.
+    Defaults: 256x256 points, S8 (40 directions), 20 steps of dt = 0.005."""
+    def st(x, rng):
+        inside = np.all((x >= 0.4) & (x <= 0.6), axis=1)
+        return np.where(inside, 100.0, 1.0)
+
+    def ss(x, rng, sig_t):
+        return ratio * sig_t
+
+    def qq(x, rng):
+        return np.where(x[:, 0] < 0.5, 1.0, 0.0)
+    return make_problem(f"2d-two-region-{n_per_dim}x{n_per_dim}-S{sn}", n_per_dim, 2, sn,
+                        seed, st, ss, qq, dt, steps)
+
+
+def lognormal_3d(n_per_dim: int = 40, sn: int = 8, seed: int = 3000, steps: int = 10,
+                 dt: float = 0.01):
+    """3D unit cube, jittered lattice, S_sn, sigma_t ~ lognormal(0, 1) per point,
+    sigma_s = 0.8 sigma_t, no volume source, isotropic inflow psi_b = 1 on the
+    x = 0 face.  Defaults: 40^3 points, S8 (80 directions), 10 steps of 0.01."""
+    def st(x, rng):
+        return rng.lognormal(0.0, 1.0, size=x.shape[0])
+
+    def ss(x, rng, sig_t):
+        return 0.8 * sig_t
+    return make_problem(f"3d-lognormal-{n_per_dim}^3-S{sn}", n_per_dim, 3, sn, seed,
+                        st, ss, 0.0, dt, steps, inflow={0: 1.0})
