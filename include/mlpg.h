@@ -1,0 +1,181 @@
+/*
+ * mlpg.h - C ABI of the GB300 (sm_103a) library for the time-dependent
+ * discrete-ordinates transport solve on a meshless MLPG discretisation with
+ * reproducing-kernel (RK) functions integrated over Voronoi-like cells
+ * (Bassett & Owen, arXiv 2008.02205).
+ *
+ * Call order: mlpg_create -> mlpg_integrate -> mlpg_assemble -> mlpg_step* ->
+ * mlpg_scalar_flux; mlpg_destroy at any time.  A call out of order returns
+ * MLPG_ERR_STATE.  No call aborts or throws: each returns a status and, on
+ * failure, mlpg_last_error() describes it.  Inputs are copied at create; the
+ * caller keeps ownership of every pointer it passes.  Host-pointer variants
+ * copy through pinned staging on the library stream; `_dev` variants take
+ * device pointers valid on the device that was current at create.
+ *
+ * All arrays are row-major.  Angular fluxes use the layout psi[i][m] (point i,
+ * direction m; the direction index varies fastest).
+ */
+#ifndef MLPG_H
+#define MLPG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlpg_ctx mlpg_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    MLPG_OK = 0,
+    MLPG_ERR_ARG = -1,           /* invalid argument (null pointer, bad size, bad enum) */
+    MLPG_ERR_STATE = -2,         /* call out of order */
+    MLPG_ERR_OOM = -3,           /* device or host allocation failed */
+    MLPG_ERR_CUDA = -4,          /* CUDA runtime error (message in mlpg_last_error) */
+    MLPG_ERR_GEOMETRY = -5,      /* a cell could not be built (point outside the box, ...) */
+    MLPG_ERR_RK_SINGULAR = -6,   /* an RK moment matrix is singular: too few neighbours */
+    MLPG_ERR_NOT_CONVERGED = -7  /* a Krylov solve hit its iteration cap */
+} mlpg_status;
+
+typedef enum {
+    MLPG_FP64 = 0,  /* every step in FP64 */
+    MLPG_MIXED = 1  /* FP32 operator streams and Krylov vectors; FP64 RK inversion,
+                       Arnoldi scalars, Hessenberg least squares and step residuals
+                       (iterative refinement of each backward-Euler step) */
+} mlpg_precision;
+
+typedef struct {
+    int dim;               /* spatial dimension: 2 */
+    double lo[3], hi[3];   /* axis-aligned box domain */
+    double tau_factor;     /* SUPG tau_i = tau_factor * h_i, h_i = R_i / 2 (Sec. 4.1); default 1 */
+    double c;              /* speed of light in 1/(c dt) (Sec. 4.1); default 1 */
+    int precision;         /* mlpg_precision; default MLPG_FP64 */
+    double inner_tol;      /* per-direction transport GMRES: ||r|| <= tol ||b||; default 1e-12 */
+    double outer_tol;      /* scattering GMRES on Phi (Eq. krylov-operator); default 1e-12 */
+    int inner_restart;     /* inner GMRES restart length (<= 64); default 30 */
+    int outer_restart;     /* outer GMRES restart length (<= 128); default 60 */
+    int max_inner;         /* inner iteration cap per solve; default 2000 */
+    int max_outer;         /* outer iteration cap per solve; default 500 */
+    double refine_tol;     /* MLPG_MIXED: FP64 step residual ||R|| <= tol ||f||; default 1e-11 */
+    int max_refine;        /* MLPG_MIXED: refinement sweeps per step; default 12 */
+    double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-5 */
+    int check_every;       /* inner GMRES: host convergence check interval (steps); default 4 */
+    void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
+} mlpg_options;
+
+typedef struct {
+    int64_t n, nnz;              /* points, overlap-pattern entries */
+    int32_t m;                   /* directions */
+    int64_t n_volume_qp;         /* volume quadrature points (Sec. 3.2) */
+    int64_t n_boundary_qp;       /* boundary quadrature points */
+    int32_t steps;               /* backward-Euler steps taken */
+    int32_t last_outer_iters;    /* scattering GMRES iterations, last step (summed over refinements) */
+    int64_t last_inner_iters;    /* inner GMRES iterations summed over directions and solves, last step */
+    int32_t last_inner_solves;   /* batched L^{-1} applications in the last step */
+    int32_t last_refinements;    /* MLPG_MIXED: refinement sweeps in the last step */
+    double last_residual;        /* final relative step residual (FP64) of the last step */
+    int64_t total_outer_iters, total_inner_iters;
+    int64_t spmm_launches;       /* batched L-apply launches since create */
+    double spmm_ms;              /* their device time (when timing is enabled), ms */
+    int64_t spmm_bytes;          /* algorithmic bytes of one batched L-apply (active precision) */
+} mlpg_stats;
+
+/* Default options (values listed in mlpg_options). */
+void mlpg_default_options(mlpg_options *opt);
+
+/* Create a problem (Sec. 4.1, Eq. transport-equation with the discrete
+ * ordinates of Sec. 4.1):
+ *   points[n*dim]        point positions x_i (inside the box)
+ *   kernel_extent[n]     kernel support radius R_i (cubic spline, h_i = R_i/2)
+ *   omega[m*3], w[m]     ordinates Omega_m (unit vectors) and weights, sum w = 4 pi
+ *   sigma_t[n], sigma_s[n], q[n]
+ *                        total / scattering cross sections and isotropic source
+ *                        per steradian, constant over each point's cell
+ * Host pointers.  Fails with MLPG_ERR_ARG on bad sizes or non-finite values.  */
+mlpg_status mlpg_create(const mlpg_options *opt, int64_t n, const double *points,
+                        const double *kernel_extent, int32_t m, const double *omega,
+                        const double *w, const double *sigma_t, const double *sigma_s,
+                        const double *q, mlpg_ctx **out);
+
+/* Same as mlpg_create with every array a device pointer. */
+mlpg_status mlpg_create_dev(const mlpg_options *opt, int64_t n, const double *points,
+                            const double *kernel_extent, int32_t m, const double *omega,
+                            const double *w, const double *sigma_t, const double *sigma_s,
+                            const double *q, mlpg_ctx **out);
+
+/* Incoming isotropic angular flux psi_b on box face `face` (0:-x 1:+x 2:-y
+ * 3:+y), Eq. rad-boundary.  Default 0 (vacuum).  Any state after create. */
+mlpg_status mlpg_set_inflow(mlpg_ctx *ctx, int face, double psi_b);
+
+/* Initial angular flux coefficients Psi_i(0) = psi_init(x_i) (Sec. 4.1), host
+ * psi0[n*m] in [i][m] layout; NULL = 0.  Any state after create. */
+mlpg_status mlpg_set_initial(mlpg_ctx *ctx, const double *psi0);
+
+/* Neighbour search (Sec. 3.4, overlap connectivity), Voronoi-like cells and
+ * their quadrature points (Sec. 3.1-3.2, App. A), RK point interpolation at
+ * the centres (Eq. flux-expansion).  MLPG_ERR_RK_SINGULAR if an RK moment
+ * matrix is singular, MLPG_ERR_GEOMETRY if a cell is empty. */
+mlpg_status mlpg_integrate(mlpg_ctx *ctx);
+
+/* Quadrature-outermost integration of every bilinear / linear form of the
+ * SUPG weak transport equation (Alg. 1, Eq. weak-transport). */
+mlpg_status mlpg_assemble(mlpg_ctx *ctx);
+
+/* One backward-Euler step (Sec. 4.1) solved as in Sec. 4.2: first-flight
+ * batched transport solves, GMRES on the scalar-flux coefficients
+ * (Eq. krylov-operator) whose operator applies the batched transport solve,
+ * angular recovery.  dt = INFINITY solves the steady problem.  Changing dt
+ * only re-forms the operators.  MLPG_ERR_NOT_CONVERGED on an iteration cap. */
+mlpg_status mlpg_step(mlpg_ctx *ctx, double dt);
+
+/* Scalar flux: kind 0 = point values phi_i = sum_j V_j U_j(x_i) Phi_j
+ * (Eq. flux-expansion), kind 1 = coefficients Phi_i.  out[n], host. */
+mlpg_status mlpg_scalar_flux(mlpg_ctx *ctx, double *out, int kind);
+
+/* Same with a device pointer; ordered on the library stream. */
+mlpg_status mlpg_scalar_flux_dev(mlpg_ctx *ctx, double *out, int kind);
+
+/* Angular flux coefficients Psi[n*m] ([i][m] layout), host; and restore. */
+mlpg_status mlpg_get_state(const mlpg_ctx *ctx, double *psi);
+mlpg_status mlpg_set_state(mlpg_ctx *ctx, const double *psi);
+
+mlpg_status mlpg_get_stats(const mlpg_ctx *ctx, mlpg_stats *stats);
+
+/* Enable device timing of the batched L-apply launches (CUDA events on the
+ * library stream); the totals appear in mlpg_stats.spmm_ms. */
+mlpg_status mlpg_enable_timing(mlpg_ctx *ctx, int on);
+
+/* ---- stage outputs, for inspection and parity checks -------------------- */
+
+/* Overlap pattern (Sec. 3.4): rowptr[n+1], col[nnz], columns ascending. */
+mlpg_status mlpg_get_neighbors(const mlpg_ctx *ctx, int64_t *rowptr, int32_t *col);
+
+/* Cell volumes V_i (Sec. 3.1), host out[n]. */
+mlpg_status mlpg_get_volumes(const mlpg_ctx *ctx, double *out);
+
+/* Number of integrated matrices / vectors and their values in this order:
+ *   matrices (nnz each): M0, Mt, Ms, G^a (dim), Gt^a (dim), Gs^a (dim),
+ *                        K^ab (dim*dim, a-major), S_f (2*dim)
+ *   vectors (n each):    Q0, Q^a (dim), B_f (2*dim)
+ * with test function U_i (row) and trial function V_j U_j (column):
+ *   M0 <U_i,V_jU_j>, Mt/Ms with sigma_t/sigma_s, G^a <d_a U_i, V_jU_j>,
+ *   K^ab <d_a U_i, d_b V_jU_j>, S_f (U_i, V_jU_j) on face f, Q0 <U_i,q>,
+ *   Q^a <d_a U_i, q>, B_f (U_i, 1) on face f.  Host out arrays. */
+int mlpg_n_matrices(int dim);
+int mlpg_n_vectors(int dim);
+mlpg_status mlpg_get_forms(const mlpg_ctx *ctx, double *mats, double *vecs);
+
+/* Batched transport operator (Sec. 4.2, operator L): Y[i][m] = (L_m X_m)_i
+ * for all directions at once, for the 1/(c dt) of `dt`; X, Y device [n][m]
+ * arrays of `precision` (MLPG_FP64: double, MLPG_MIXED: float). */
+mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void *X, void *Y);
+
+/* Last error message of this context ("" when none). */
+const char *mlpg_last_error(const mlpg_ctx *ctx);
+
+void mlpg_destroy(mlpg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLPG_H */

@@ -1,0 +1,189 @@
+// Internal declarations of the MLPG transport library (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "mlpg.h"
+
+#define MLPG_MAX_DIR 1024   // directions per problem (one thread per direction in a block row)
+#define MLPG_MAX_RESTART 64 // inner / outer restart length cap for the device Hessenberg arrays
+#define MLPG_MAX_CELL_FUNCS 40  // functions whose support can reach one 2D cell
+
+namespace mlpg {
+
+// error helpers --------------------------------------------------------------
+#define MLPG_TRY(expr)                         \
+    do {                                       \
+        mlpg_status _s = (expr);               \
+        if (_s != MLPG_OK) return _s;          \
+    } while (0)
+
+mlpg_status cuda_fail(mlpg_ctx *ctx, cudaError_t e, const char *what, const char *file, int line);
+#define CU(ctx, expr)                                                               \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) return mlpg::cuda_fail((ctx), _e, #expr, __FILE__, __LINE__); \
+    } while (0)
+#define CU_LAUNCH(ctx) CU(ctx, cudaGetLastError())
+
+// host geometry (geometry.cpp) ----------------------------------------------
+struct HostCells {
+    std::vector<int32_t> cptr;      // n + 1
+    std::vector<double> verts;      // 2 * nv
+    std::vector<int32_t> labels;    // nv: >= 0 bisector, -(f+1) domain face, LABEL_EXTENT
+    std::vector<double> volume;     // n
+    int64_t n_volume_qp = 0, n_boundary_qp = 0;
+};
+constexpr int32_t kLabelExtent = -100;
+// Builds the cells of all points; returns the index of a failing cell or -1.
+int64_t build_cells_2d(int64_t n, const double *x, const double *R, const double *lo,
+                       const double *hi, const int32_t *rowptr, const int32_t *col,
+                       int tri_points, int line_points, HostCells &out);
+// Reference rules (quadrature.cpp).
+void gauss_jacobi_newton(int n, double a, double b, double *t, double *w);
+void triangle_rule(int n1d, double *xi /*2*n1d^2*/, double *w);
+void line_rule(int n, double *t, double *w);
+
+// GMRES workspace ------------------------------------------------------------
+template <typename T>
+struct Gmres {
+    int64_t n = 0;
+    int M = 0, R = 0;
+    T *V = nullptr;        // (R + 1) * n * M
+    T *Z = nullptr;        // n * M: preconditioned basis vector
+    T *W = nullptr;        // n * M: scratch for true residuals
+    double *H = nullptr;   // M * (R + 1) * R
+    double *cs = nullptr, *sn = nullptr;   // M * R
+    double *g = nullptr;   // M * (R + 1)
+    double *h = nullptr;   // (R + 1) * M : dot results of the current step
+    double *h2 = nullptr;  // (R + 1) * M
+    double *y = nullptr;   // R * M
+    double *bnorm = nullptr, *beta = nullptr, *resid = nullptr;  // M
+    int *active = nullptr; // M: 1 while iterating in this cycle
+    int *kcol = nullptr;   // M: Arnoldi columns used in this cycle
+    int *its = nullptr;    // M: total iterations
+    double *partial = nullptr; // reduction partials
+    int64_t partial_cap = 0;
+    int *h_active = nullptr;   // pinned host mirror: number of active directions
+    int *d_active_count = nullptr;
+};
+
+}  // namespace mlpg
+
+struct mlpg_ctx {
+    mlpg_options opt{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    int state = 0;  // 0 created, 1 integrated, 2 assembled
+    int64_t n = 0;
+    int m = 0, dim = 2;
+    std::vector<void *> allocs;       // device allocations
+    std::vector<void *> host_allocs;  // pinned host allocations
+
+    // inputs (device)
+    double *x = nullptr, *R = nullptr, *V = nullptr, *sig_t = nullptr, *sig_s = nullptr,
+           *q = nullptr, *omega = nullptr, *w = nullptr, *tau = nullptr;
+    std::vector<double> h_x, h_R, h_omega, h_w;
+    double psi_b[6] = {0, 0, 0, 0, 0, 0};
+    bool have_initial = false;
+
+    // connectivity
+    int64_t nnz = 0;
+    int32_t *rowptr = nullptr, *col = nullptr, *diag = nullptr;
+    std::vector<int32_t> h_rowptr, h_col;
+
+    // cells
+    int64_t nverts = 0, nvq = 0, nbq = 0;
+    int32_t *cptr = nullptr, *labels = nullptr;
+    double *verts = nullptr;
+    double *interp = nullptr;   // [nnz]: V_j U_j(x_i) on the overlap pattern
+    int *d_flag = nullptr;      // device error flag (assembly / RK)
+
+    // integrated forms (FP64)
+    double *mats = nullptr, *vecs = nullptr;
+    int nmats = 0, nvecs = 0;
+
+    // operators for the current 1/(c dt)
+    double kappa = -1.0;
+    double *A64 = nullptr;      // [6][nnz] direction-independent LHS arrays
+    double *L64 = nullptr;      // [nnz][m] materialised per-direction L_m (FP64 path)
+    float *A32 = nullptr;       // [6][nnz]
+    int64_t nb = 0;             // boundary-segment entries
+    int32_t *bptr = nullptr, *bcol = nullptr;
+    float *bval32 = nullptr;    // [2 dim][nb]
+    double *bval64 = nullptr;   // [2 dim][nb]
+    double *coef = nullptr;     // [m][8]: 1, Ox, Oy, Ox^2, Oy^2, OxOy, (unused x2)
+    double *fcoef = nullptr;    // [m][2 dim]: max(Omega . n_f, 0)
+    double *dinv64 = nullptr;   // [n][m]
+    float *dinv32 = nullptr;
+    double *r64 = nullptr;      // [n][m] boundary + volume source
+    double *T64 = nullptr;      // [3][nnz]: kappa M0, kappa tau G^x, kappa tau G^y
+    double *S64 = nullptr;      // [3][nnz]: Ms, tau Gs^x, tau Gs^y
+
+    // state and work
+    double *Psi = nullptr, *Phi = nullptr;   // [n][m], [n]
+    double *f64 = nullptr, *res64 = nullptr, *tmp64 = nullptr;  // [n][m]
+    double *bpsi64 = nullptr;                // [n][m]
+    float *rhs32 = nullptr, *sol32 = nullptr, *bpsi32 = nullptr;  // [n][m]
+    double *rhs64b = nullptr, *sol64 = nullptr;   // [n][m]
+    double *nvec = nullptr;                  // [8][n] small n-vectors
+    double *red = nullptr;                   // reduction scratch
+    int64_t red_cap = 0;
+    double *h_red = nullptr;                 // pinned host scalars
+
+    mlpg::Gmres<double> g64;
+    mlpg::Gmres<float> g32;
+    mlpg::Gmres<double> gout;
+
+    double ops_psib[6] = {0, 0, 0, 0, 0, 0};  // inflow the operators were formed with
+    int32_t *rowidx = nullptr;  // [nnz] row of each pattern entry
+    double *abc = nullptr;      // [3][n] MS partial products
+    double cur_inner_tol = 0.0; // tolerance of the inner solves inside the outer operator
+
+    // stats
+    mlpg_stats st{};
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    int ev_used = 0;
+};
+
+namespace mlpg {
+mlpg_status set_err(mlpg_ctx *ctx, mlpg_status s, const std::string &msg);
+template <typename T>
+mlpg_status dalloc(mlpg_ctx *ctx, T **p, size_t count) {
+    void *q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(ctx, MLPG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    ctx->allocs.push_back(q);
+    *p = static_cast<T *>(q);
+    return MLPG_OK;
+}
+
+// kernels / launchers (neighbors.cu, assemble.cu, operators.cu, krylov.cu)
+mlpg_status run_neighbors(mlpg_ctx *ctx);
+mlpg_status run_interp(mlpg_ctx *ctx);
+mlpg_status run_assemble(mlpg_ctx *ctx);
+mlpg_status form_operators(mlpg_ctx *ctx, double kappa);
+mlpg_status apply_L64(mlpg_ctx *ctx, const double *X, double *Y);
+mlpg_status apply_L32(mlpg_ctx *ctx, const float *X, float *Y);
+mlpg_status step_fp64(mlpg_ctx *ctx, double dt);
+mlpg_status step_mixed(mlpg_ctx *ctx, double dt);
+mlpg_status apply_L64_res(mlpg_ctx *ctx, const double *X, const double *B, double *Y);
+mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *Y);
+mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F);
+template <typename T>
+mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out);
+mlpg_status interp_flux(mlpg_ctx *ctx, double *out_dev, int kind);
+void harvest_timing(mlpg_ctx *ctx);
+}  // namespace mlpg

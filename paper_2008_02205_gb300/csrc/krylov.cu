@@ -1,0 +1,611 @@
+// Krylov solves of one backward-Euler step (Sec. 4.2).
+//
+// Batched GMRES: M independent systems advance together.  Vectors use the
+// layout v[i][m] (system index fastest).  Each system has its own Hessenberg
+// matrix, Givens rotations, residual estimate and convergence mask, all kept
+// on the device; the host only polls the number of systems still iterating
+// every few Arnoldi steps.  Orthogonalisation is classical Gram-Schmidt applied
+// twice (CGS2); dot products are accumulated in FP64 whatever the vector type.
+// Right preconditioning by the inverse diagonal (Jacobi) of each L_m.
+//
+// The same engine with M = 1 and no preconditioner runs the scattering
+// iteration on the scalar-flux coefficients, Eq. krylov-operator:
+//   (I - D L^{-1} MS) Phi = D L^{-1} (T Psi^{n-1} + r),
+// whose operator apply is one batched transport solve (all directions).
+#include <algorithm>
+#include <cmath>
+#include <functional>
+
+#include "internal.h"
+
+namespace mlpg {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct Map2 {       // (direction, row) mapping of a 256-thread block
+    int MB, RB, mchunks;
+};
+Map2 map2(int M) {
+    Map2 r;
+    r.MB = M <= kBlock ? M : kBlock;
+    r.RB = kBlock / r.MB;
+    r.mchunks = (M + r.MB - 1) / r.MB;
+    return r;
+}
+int grid_rows(int64_t n, const Map2 &mp, int nl) {
+    int64_t maxg = (n + mp.RB - 1) / mp.RB;
+    int64_t g = (1216 + mp.mchunks * nl - 1) / (mp.mchunks * nl);
+    if (g > maxg) g = maxg;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// partial[(l * G + block) * M + m] = sum over this block's rows of V_l[i][m] * w[i][m]
+template <typename T>
+__global__ void k_dots(int64_t n, int M, int MB, int RB, const T *__restrict__ V, int64_t vstride,
+                       const T *__restrict__ w, double *__restrict__ partial) {
+    extern __shared__ double sh[];
+    const int t = threadIdx.x, ml = t % MB, r = t / MB;
+    const int m = blockIdx.y * MB + ml, l = blockIdx.z, G = gridDim.x;
+    double acc = 0.0;
+    if (r < RB && m < M) {
+        const T *v = V + l * vstride;
+        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += (int64_t)G * RB) {
+            int64_t e = i * M + m;
+            acc += (double)v[e] * (double)w[e];
+        }
+    }
+    sh[t] = acc;
+    __syncthreads();
+    if (r == 0 && m < M) {
+        double s = 0.0;
+        for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
+        partial[((int64_t)l * G + blockIdx.x) * M + m] = s;
+    }
+}
+
+// out[l][m] = sum_g partial[l][g][m]   (fixed order: deterministic)
+__global__ void k_reduce(int M, int nl, int G, const double *__restrict__ partial, double *__restrict__ out) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * nl) return;
+    int l = e / M, m = e - l * M;
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += partial[((int64_t)l * G + g) * M + m];
+    out[e] = s;
+}
+
+// w[i][m] -= sum_{l < nl} h[l][m] V_l[i][m]
+template <typename T>
+__global__ void k_update(int64_t n, int M, int nl, const T *__restrict__ V, int64_t vstride,
+                         const double *__restrict__ h, T *__restrict__ w) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * M) return;
+    int m = (int)(e % M);
+    double s = (double)w[e];
+    for (int l = 0; l < nl; ++l) s -= h[l * M + m] * (double)V[l * vstride + e];
+    w[e] = (T)s;
+}
+
+// as k_update, and partial sums of the squared result (norm)
+template <typename T>
+__global__ void k_update_norm(int64_t n, int M, int MB, int RB, int nl, const T *__restrict__ V,
+                              int64_t vstride, const double *__restrict__ h, T *__restrict__ w,
+                              double *__restrict__ partial) {
+    extern __shared__ double sh[];
+    const int t = threadIdx.x, ml = t % MB, r = t / MB;
+    const int m = blockIdx.y * MB + ml, G = gridDim.x;
+    double acc = 0.0;
+    if (r < RB && m < M) {
+        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += (int64_t)G * RB) {
+            int64_t e = i * M + m;
+            double s = (double)w[e];
+            for (int l = 0; l < nl; ++l) s -= h[l * M + m] * (double)V[l * vstride + e];
+            T st = (T)s;
+            w[e] = st;
+            acc += (double)st * (double)st;
+        }
+    }
+    sh[t] = acc;
+    __syncthreads();
+    if (r == 0 && m < M) {
+        double s = 0.0;
+        for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
+        partial[(int64_t)blockIdx.x * M + m] = s;
+    }
+}
+
+// Start of a cycle: beta = ||r|| from partials; decide which systems iterate.
+__global__ void k_start(int M, int G, int R, const double *__restrict__ partial, double *__restrict__ bnorm,
+                        double *__restrict__ g, double *__restrict__ sc, int *__restrict__ active,
+                        int *__restrict__ kcol, double *__restrict__ resid, double tol, int set_bnorm,
+                        int *__restrict__ count) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double s = 0.0;
+    for (int k = 0; k < G; ++k) s += partial[(int64_t)k * M + m];
+    double beta = sqrt(s);
+    if (set_bnorm) bnorm[m] = beta;
+    resid[m] = beta;
+    kcol[m] = 0;
+    bool act = beta > tol * bnorm[m] && beta > 0.0;
+    active[m] = act;
+    g[m * (R + 1)] = beta;
+    for (int k = 1; k <= R; ++k) g[m * (R + 1) + k] = 0.0;
+    sc[m] = act ? 1.0 / beta : 0.0;
+    if (act) atomicAdd(count, 1);
+}
+
+// Column j of the Hessenberg matrix, Givens rotations, residual estimate.
+__global__ void k_givens(int M, int G, int R, int j, const double *__restrict__ h1,
+                         const double *__restrict__ h2, const double *__restrict__ partial,
+                         double *__restrict__ H, double *__restrict__ cs, double *__restrict__ sn,
+                         double *__restrict__ g, double *__restrict__ sc, int *__restrict__ active,
+                         int *__restrict__ kcol, int *__restrict__ its, double *__restrict__ resid,
+                         const double *__restrict__ bnorm, double tol, int *__restrict__ count) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    if (!active[m]) {
+        sc[m] = 0.0;
+        return;
+    }
+    double s = 0.0;
+    for (int k = 0; k < G; ++k) s += partial[(int64_t)k * M + m];
+    double hn = sqrt(s);
+    double *Hm = H + (int64_t)m * (R + 1) * R;  // Hm[row * R + col]
+    for (int l = 0; l <= j; ++l) Hm[l * R + j] = h1[l * M + m] + h2[l * M + m];
+    Hm[(j + 1) * R + j] = hn;
+    for (int l = 0; l < j; ++l) {
+        double c = cs[m * R + l], sv = sn[m * R + l];
+        double a = Hm[l * R + j], b = Hm[(l + 1) * R + j];
+        Hm[l * R + j] = c * a + sv * b;
+        Hm[(l + 1) * R + j] = -sv * a + c * b;
+    }
+    double a = Hm[j * R + j], b = Hm[(j + 1) * R + j];
+    double den = hypot(a, b);
+    double c = den > 0.0 ? a / den : 1.0, sv = den > 0.0 ? b / den : 0.0;
+    cs[m * R + j] = c;
+    sn[m * R + j] = sv;
+    Hm[j * R + j] = den;
+    Hm[(j + 1) * R + j] = 0.0;
+    double gj = g[m * (R + 1) + j];
+    g[m * (R + 1) + j] = c * gj;
+    g[m * (R + 1) + j + 1] = -sv * gj;
+    its[m] += 1;
+    kcol[m] = j + 1;
+    double res = fabs(sv * gj);
+    resid[m] = res;
+    bool done = res <= tol * bnorm[m] || !(hn > 0.0) || j + 1 == R;
+    if (done) {
+        active[m] = 0;
+        sc[m] = 0.0;
+    } else {
+        sc[m] = 1.0 / hn;
+        atomicAdd(count, 1);
+    }
+}
+
+// v = w * sc[m]; z = v * dinv (or v)
+template <typename T>
+__global__ void k_scale(int64_t n, int M, T *__restrict__ w, const double *__restrict__ sc,
+                        const T *__restrict__ dinv, T *__restrict__ z) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * M) return;
+    int m = (int)(e % M);
+    double v = (double)w[e] * sc[m];
+    w[e] = (T)v;
+    z[e] = dinv ? (T)(v * (double)dinv[e]) : (T)v;
+}
+
+// y = R^{-1} g per system (upper triangular part of the rotated Hessenberg)
+__global__ void k_backsolve(int M, int R, const double *__restrict__ H, const double *__restrict__ g,
+                            const int *__restrict__ kcol, double *__restrict__ y) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int k = kcol[m];
+    const double *Hm = H + (int64_t)m * (R + 1) * R;
+    for (int r = k - 1; r >= 0; --r) {
+        double s = g[m * (R + 1) + r];
+        for (int c = r + 1; c < k; ++c) s -= Hm[r * R + c] * y[c * M + m];
+        y[r * M + m] = Hm[r * R + r] != 0.0 ? s / Hm[r * R + r] : 0.0;
+    }
+}
+
+// x += dinv * sum_{l < kcol[m]} y_l V_l
+template <typename T>
+__global__ void k_xupdate(int64_t n, int M, int kmax, const T *__restrict__ V, int64_t vstride,
+                          const double *__restrict__ y, const int *__restrict__ kcol,
+                          const T *__restrict__ dinv, T *__restrict__ x) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * M) return;
+    int m = (int)(e % M);
+    int k = kcol[m];
+    if (k == 0) return;
+    double s = 0.0;
+    for (int l = 0; l < kmax && l < k; ++l) s += y[l * M + m] * (double)V[l * vstride + e];
+    if (dinv) s *= (double)dinv[e];
+    x[e] = (T)((double)x[e] + s);
+}
+
+// out[i] = sum_m w[m] x[i][m]  (angular reduction D, Sec. 4.2)
+template <typename T>
+__global__ void k_Dreduce(int64_t n, int M, const double *__restrict__ w, const T *__restrict__ x,
+                          double *__restrict__ out) {
+    int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int m = lane; m < M; m += 32) s += w[m] * (double)x[i * M + m];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(int64_t N, const Ti *__restrict__ a, To *__restrict__ b) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < N) b[e] = (To)a[e];
+}
+
+// c = a + b (mixed types; c may alias a)
+template <typename Ta, typename Tb>
+__global__ void k_add(int64_t N, const Ta *a, const Tb *__restrict__ b, double *c) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < N) c[e] = (double)a[e] + (double)b[e];
+}
+
+// y = B - (X - d)   or   y = X - d       (outer operator I - D L^{-1} MS)
+__global__ void k_outer_combine(int64_t n, const double *__restrict__ X, const double *__restrict__ d,
+                                const double *__restrict__ B, double *__restrict__ Y) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = X[i] - d[i];
+    Y[i] = B ? B[i] - v : v;
+}
+
+// partial sums of squares over N elements (for global norms)
+__global__ void k_sumsq(int64_t N, const double *__restrict__ a, double *__restrict__ partial) {
+    __shared__ double sh[kBlock];
+    double s = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N; e += (int64_t)gridDim.x * blockDim.x)
+        s += a[e] * a[e];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = kBlock / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+inline int64_t nblk(int64_t N) { return (N + kBlock - 1) / kBlock; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+template <typename T>
+static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int R) {
+    if (G.n == n && G.M == M && G.R == R) return MLPG_OK;
+    if (R > MLPG_MAX_RESTART || R < 1) return set_err(ctx, MLPG_ERR_ARG, "restart length out of range");
+    G.n = n; G.M = M; G.R = R;
+    MLPG_TRY(dalloc(ctx, &G.V, (size_t)(R + 1) * n * M));
+    MLPG_TRY(dalloc(ctx, &G.Z, (size_t)n * M));
+    MLPG_TRY(dalloc(ctx, &G.W, (size_t)n * M));
+    MLPG_TRY(dalloc(ctx, &G.H, (size_t)M * (R + 1) * R));
+    MLPG_TRY(dalloc(ctx, &G.cs, (size_t)M * R));
+    MLPG_TRY(dalloc(ctx, &G.sn, (size_t)M * R));
+    MLPG_TRY(dalloc(ctx, &G.g, (size_t)M * (R + 1)));
+    MLPG_TRY(dalloc(ctx, &G.h, (size_t)(R + 1) * M));
+    MLPG_TRY(dalloc(ctx, &G.h2, (size_t)(R + 1) * M));
+    MLPG_TRY(dalloc(ctx, &G.y, (size_t)R * M));
+    MLPG_TRY(dalloc(ctx, &G.bnorm, M));
+    MLPG_TRY(dalloc(ctx, &G.beta, M));   // scale factors 1/||w||
+    MLPG_TRY(dalloc(ctx, &G.resid, M));
+    MLPG_TRY(dalloc(ctx, &G.active, M));
+    MLPG_TRY(dalloc(ctx, &G.kcol, M));
+    MLPG_TRY(dalloc(ctx, &G.its, M));
+    G.partial_cap = (int64_t)1300 * M;
+    MLPG_TRY(dalloc(ctx, &G.partial, G.partial_cap));
+    MLPG_TRY(dalloc(ctx, &G.d_active_count, 1));
+    void *hp = nullptr;
+    CU(ctx, cudaHostAlloc(&hp, sizeof(int) * 4, cudaHostAllocDefault));
+    ctx->host_allocs.push_back(hp);
+    G.h_active = (int *)hp;
+    return MLPG_OK;
+}
+
+template <typename T>
+using ApplyFn = std::function<mlpg_status(const T *X, const T *B, T *Y)>;
+
+// Solve A x = b for all M systems; x holds the initial guess.  Returns the
+// summed iteration count in *iters and MLPG_ERR_NOT_CONVERGED on the cap.
+template <typename T>
+static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, const T *dinv, const T *b,
+                               T *x, double tol, int max_its, int check_every, int64_t *iters) {
+    const int64_t n = G.n, N = n * G.M;
+    const int M = G.M, R = G.R;
+    const int64_t vs = N;
+    cudaStream_t s = ctx->stream;
+    const Map2 mp = map2(M);
+    CU(ctx, cudaMemsetAsync(G.its, 0, sizeof(int) * M, s));
+    int64_t total = 0;
+    for (int cycle = 0;; ++cycle) {
+        // r = b - A x  -> V_0
+        MLPG_TRY(A(x, b, G.V));
+        int g1 = grid_rows(n, mp, 1);
+        if (cycle == 0) {
+            // ||b|| first (into bnorm via k_start with set_bnorm)
+            k_dots<T><<<dim3(g1, mp.mchunks, 1), kBlock, kBlock * sizeof(double), s>>>(n, M, mp.MB, mp.RB, b, 0, b,
+                                                                                     G.partial);
+            CU_LAUNCH(ctx);
+            CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
+            k_start<<<(M + 127) / 128, 128, 0, s>>>(M, g1, R, G.partial, G.bnorm, G.g, G.beta, G.active, G.kcol,
+                                                    G.resid, 0.0, 1, G.d_active_count);
+            CU_LAUNCH(ctx);
+        }
+        k_dots<T><<<dim3(g1, mp.mchunks, 1), kBlock, kBlock * sizeof(double), s>>>(n, M, mp.MB, mp.RB, G.V, 0, G.V,
+                                                                                 G.partial);
+        CU_LAUNCH(ctx);
+        CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
+        k_start<<<(M + 127) / 128, 128, 0, s>>>(M, g1, R, G.partial, G.bnorm, G.g, G.beta, G.active, G.kcol,
+                                                G.resid, tol, 0, G.d_active_count);
+        CU_LAUNCH(ctx);
+        CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+        if (*G.h_active == 0) break;
+        if (total >= (int64_t)max_its * M) {
+            *iters = total;
+            return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
+        }
+        k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, G.V, G.beta, dinv, G.Z);
+        CU_LAUNCH(ctx);
+        int jlast = 0;
+        for (int j = 0; j < R; ++j) {
+            T *w = G.V + (j + 1) * vs;
+            MLPG_TRY(A(G.Z, nullptr, w));
+            for (int pass = 0; pass < 2; ++pass) {
+                double *hh = pass == 0 ? G.h : G.h2;
+                int gd = grid_rows(n, mp, j + 1);
+                k_dots<T><<<dim3(gd, mp.mchunks, j + 1), kBlock, kBlock * sizeof(double), s>>>(
+                    n, M, mp.MB, mp.RB, G.V, vs, w, G.partial);
+                CU_LAUNCH(ctx);
+                k_reduce<<<((j + 1) * M + 127) / 128, 128, 0, s>>>(M, j + 1, gd, G.partial, hh);
+                CU_LAUNCH(ctx);
+                if (pass == 0) {
+                    k_update<T><<<nblk(N), kBlock, 0, s>>>(n, M, j + 1, G.V, vs, hh, w);
+                } else {
+                    k_update_norm<T><<<dim3(g1, mp.mchunks), kBlock, kBlock * sizeof(double), s>>>(
+                        n, M, mp.MB, mp.RB, j + 1, G.V, vs, hh, w, G.partial);
+                }
+                CU_LAUNCH(ctx);
+            }
+            CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
+            k_givens<<<(M + 127) / 128, 128, 0, s>>>(M, g1, R, j, G.h, G.h2, G.partial, G.H, G.cs, G.sn, G.g,
+                                                     G.beta, G.active, G.kcol, G.its, G.resid, G.bnorm, tol,
+                                                     G.d_active_count);
+            CU_LAUNCH(ctx);
+            k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, w, G.beta, dinv, G.Z);
+            CU_LAUNCH(ctx);
+            jlast = j;
+            if ((j + 1) % check_every == 0 || j + 1 == R) {
+                CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+                CU(ctx, cudaStreamSynchronize(s));
+                if (*G.h_active == 0) break;
+            }
+        }
+        k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y);
+        CU_LAUNCH(ctx);
+        k_xupdate<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, G.y, G.kcol, dinv, x);
+        CU_LAUNCH(ctx);
+        // iterations of this cycle
+        std::vector<int> its(M);
+        CU(ctx, cudaMemcpyAsync(its.data(), G.its, sizeof(int) * M, cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+        total = 0;
+        for (int v : its) total += v;
+    }
+    *iters = total;
+    return MLPG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one batched transport solve L_m x_m = b_m, all directions (x0 = 0)
+// ---------------------------------------------------------------------------
+template <typename T>
+static mlpg_status inner_solve(mlpg_ctx *ctx, const T *b, T *x, double tol);
+
+template <>
+mlpg_status inner_solve<double>(mlpg_ctx *ctx, const double *b, double *x, double tol) {
+    MLPG_TRY(gmres_alloc(ctx, ctx->g64, ctx->n, ctx->m, ctx->opt.inner_restart));
+    CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * ctx->n * ctx->m, ctx->stream));
+    ApplyFn<double> A = [ctx](const double *X, const double *B, double *Y) { return apply_L64_res(ctx, X, B, Y); };
+    int64_t its = 0;
+    mlpg_status st = gmres_solve<double>(ctx, ctx->g64, A, ctx->dinv64, b, x, tol, ctx->opt.max_inner,
+                                         ctx->opt.check_every, &its);
+    ctx->st.last_inner_iters += its;
+    ctx->st.last_inner_solves += 1;
+    return st;
+}
+
+template <>
+mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double tol) {
+    MLPG_TRY(gmres_alloc(ctx, ctx->g32, ctx->n, ctx->m, ctx->opt.inner_restart));
+    CU(ctx, cudaMemsetAsync(x, 0, sizeof(float) * ctx->n * ctx->m, ctx->stream));
+    ApplyFn<float> A = [ctx](const float *X, const float *B, float *Y) { return apply_L32_res(ctx, X, B, Y); };
+    int64_t its = 0;
+    mlpg_status st = gmres_solve<float>(ctx, ctx->g32, A, ctx->dinv32, b, x, tol, ctx->opt.max_inner,
+                                        ctx->opt.check_every, &its);
+    ctx->st.last_inner_iters += its;
+    ctx->st.last_inner_solves += 1;
+    return st;
+}
+
+static mlpg_status ensure_step_buffers(mlpg_ctx *ctx) {
+    if (ctx->f64) return MLPG_OK;
+    const size_t N = (size_t)ctx->n * ctx->m;
+    MLPG_TRY(dalloc(ctx, &ctx->f64, N));
+    MLPG_TRY(dalloc(ctx, &ctx->res64, N));
+    MLPG_TRY(dalloc(ctx, &ctx->tmp64, N));
+    MLPG_TRY(dalloc(ctx, &ctx->bpsi64, N));
+    MLPG_TRY(dalloc(ctx, &ctx->rhs64b, N));
+    MLPG_TRY(dalloc(ctx, &ctx->sol64, N));
+    MLPG_TRY(dalloc(ctx, &ctx->rhs32, N));
+    MLPG_TRY(dalloc(ctx, &ctx->sol32, N));
+    MLPG_TRY(dalloc(ctx, &ctx->bpsi32, N));
+    MLPG_TRY(dalloc(ctx, &ctx->nvec, 8 * ctx->n));
+    ctx->red_cap = 4096;
+    MLPG_TRY(dalloc(ctx, &ctx->red, ctx->red_cap));
+    void *hp = nullptr;
+    CU(ctx, cudaHostAlloc(&hp, sizeof(double) * 16, cudaHostAllocDefault));
+    ctx->host_allocs.push_back(hp);
+    ctx->h_red = (double *)hp;
+    return MLPG_OK;
+}
+
+// Nested solve of (L - MS D) Psi = f (Sec. 4.2): first flight, GMRES on Phi,
+// recovery.  f and Psi are FP64 [n][m]; inner solves run in T.  Phi_io holds
+// the initial guess of Phi on entry (may be null) and the result on exit.
+template <typename T>
+static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out, double *Phi_io,
+                                double inner_tol, double outer_tol) {
+    const int64_t n = ctx->n, N = n * ctx->m;
+    cudaStream_t s = ctx->stream;
+    T *rhs, *bpsi, *x;
+    if constexpr (sizeof(T) == 8) {
+        rhs = (T *)ctx->rhs64b;
+        bpsi = (T *)ctx->bpsi64;
+        x = (T *)ctx->sol64;
+    } else {
+        rhs = (T *)ctx->rhs32;
+        bpsi = (T *)ctx->bpsi32;
+        x = (T *)ctx->sol32;
+    }
+    double *bphi = ctx->nvec, *d = ctx->nvec + n, *phi = ctx->nvec + 2 * ctx->n;
+    k_convert<double, T><<<nblk(N), kBlock, 0, s>>>(N, f, rhs);
+    CU_LAUNCH(ctx);
+    // first flight b_psi = L^{-1} f, b_phi = D b_psi
+    MLPG_TRY(inner_solve<T>(ctx, rhs, bpsi, inner_tol));
+    k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, bpsi, bphi);
+    CU_LAUNCH(ctx);
+    // scattering GMRES: (I - D L^{-1} MS) Phi = b_phi
+    MLPG_TRY(gmres_alloc(ctx, ctx->gout, n, 1, ctx->opt.outer_restart));
+    if (Phi_io) CU(ctx, cudaMemcpyAsync(phi, Phi_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    else CU(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, s));
+    ApplyFn<double> A = [ctx, rhs, x, d, n, s](const double *X, const double *B, double *Y) -> mlpg_status {
+        MLPG_TRY(apply_MS<T>(ctx, X, rhs));
+        MLPG_TRY(inner_solve<T>(ctx, rhs, x, ctx->cur_inner_tol));
+        k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, x, d);
+        CU_LAUNCH(ctx);
+        k_outer_combine<<<nblk(n), kBlock, 0, s>>>(n, X, d, B, Y);
+        CU_LAUNCH(ctx);
+        return MLPG_OK;
+    };
+    ctx->cur_inner_tol = inner_tol;
+    int64_t oits = 0;
+    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, nullptr, bphi, phi, outer_tol, ctx->opt.max_outer, 1, &oits));
+    ctx->st.last_outer_iters += (int32_t)oits;
+    // recovery Psi = L^{-1} MS Phi + b_psi
+    MLPG_TRY(apply_MS<T>(ctx, phi, rhs));
+    MLPG_TRY(inner_solve<T>(ctx, rhs, x, inner_tol));
+    k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, x, bpsi, Psi_out);
+    CU_LAUNCH(ctx);
+    if (Phi_io) CU(ctx, cudaMemcpyAsync(Phi_io, phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    return MLPG_OK;
+}
+
+static mlpg_status global_norm(mlpg_ctx *ctx, const double *a, int64_t N, double *out_host_slot) {
+    int64_t G = std::min<int64_t>(1024, nblk(N));
+    k_sumsq<<<G, kBlock, 0, ctx->stream>>>(N, a, ctx->red);
+    CU_LAUNCH(ctx);
+    k_reduce<<<1, 128, 0, ctx->stream>>>(1, 1, (int)G, ctx->red, ctx->red + 2048);
+    CU_LAUNCH(ctx);
+    CU(ctx, cudaMemcpyAsync(out_host_slot, ctx->red + 2048, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return MLPG_OK;
+}
+
+static void reset_step_stats(mlpg_ctx *ctx) {
+    ctx->st.last_outer_iters = 0;
+    ctx->st.last_inner_iters = 0;
+    ctx->st.last_inner_solves = 0;
+    ctx->st.last_refinements = 0;
+}
+
+static mlpg_status prepare_step(mlpg_ctx *ctx, double dt) {
+    double kappa = std::isfinite(dt) ? 1.0 / (ctx->opt.c * dt) : 0.0;
+    bool same_inflow = true;
+    for (int f = 0; f < 6; ++f) same_inflow &= ctx->ops_psib[f] == ctx->psi_b[f];
+    if (kappa != ctx->kappa || !same_inflow) MLPG_TRY(form_operators(ctx, kappa));
+    MLPG_TRY(ensure_step_buffers(ctx));
+    reset_step_stats(ctx);
+    return MLPG_OK;
+}
+
+static void finish_step_stats(mlpg_ctx *ctx) {
+    ctx->st.steps += 1;
+    ctx->st.total_outer_iters += ctx->st.last_outer_iters;
+    ctx->st.total_inner_iters += ctx->st.last_inner_iters;
+}
+
+mlpg_status step_fp64(mlpg_ctx *ctx, double dt) {
+    MLPG_TRY(prepare_step(ctx, dt));
+    const int64_t n = ctx->n, N = n * ctx->m;
+    cudaStream_t s = ctx->stream;
+    MLPG_TRY(rhs_T(ctx, ctx->Psi, ctx->f64));
+    MLPG_TRY(nested_solve<double>(ctx, ctx->f64, ctx->tmp64, ctx->Phi, ctx->opt.inner_tol, ctx->opt.outer_tol));
+    CU(ctx, cudaMemcpyAsync(ctx->Psi, ctx->tmp64, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    k_Dreduce<double><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, ctx->Psi, ctx->Phi);
+    CU_LAUNCH(ctx);
+    // report the FP64 step residual
+    MLPG_TRY(apply_L64_res(ctx, ctx->Psi, ctx->f64, ctx->res64));
+    MLPG_TRY(apply_MS<double>(ctx, ctx->Phi, ctx->tmp64));
+    k_add<double, double><<<nblk(N), kBlock, 0, s>>>(N, ctx->res64, ctx->tmp64, ctx->res64);
+    CU_LAUNCH(ctx);
+    MLPG_TRY(global_norm(ctx, ctx->res64, N, ctx->h_red));
+    MLPG_TRY(global_norm(ctx, ctx->f64, N, ctx->h_red + 1));
+    CU(ctx, cudaStreamSynchronize(s));
+    ctx->st.last_residual = ctx->h_red[1] > 0 ? std::sqrt(ctx->h_red[0] / ctx->h_red[1]) : 0.0;
+    finish_step_stats(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status step_mixed(mlpg_ctx *ctx, double dt) {
+    MLPG_TRY(prepare_step(ctx, dt));
+    const int64_t n = ctx->n, N = n * ctx->m;
+    cudaStream_t s = ctx->stream;
+    MLPG_TRY(rhs_T(ctx, ctx->Psi, ctx->f64));
+    MLPG_TRY(global_norm(ctx, ctx->f64, N, ctx->h_red + 1));
+    // Psi^{(0)} = Psi^{n-1}; refine Psi += (L - MS D)^{-1}_{FP32} R
+    double *phi_c = ctx->nvec + 3 * n;
+    int k = 0;
+    double rel = 0.0;
+    for (;; ++k) {
+        k_Dreduce<double><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, ctx->Psi, phi_c);
+        CU_LAUNCH(ctx);
+        MLPG_TRY(apply_L64_res(ctx, ctx->Psi, ctx->f64, ctx->res64));
+        MLPG_TRY(apply_MS<double>(ctx, phi_c, ctx->tmp64));
+        k_add<double, double><<<nblk(N), kBlock, 0, s>>>(N, ctx->res64, ctx->tmp64, ctx->res64);
+        CU_LAUNCH(ctx);
+        MLPG_TRY(global_norm(ctx, ctx->res64, N, ctx->h_red));
+        CU(ctx, cudaStreamSynchronize(s));
+        rel = ctx->h_red[1] > 0 ? std::sqrt(ctx->h_red[0] / ctx->h_red[1]) : 0.0;
+        if (rel <= ctx->opt.refine_tol) break;
+        if (k >= ctx->opt.max_refine) {
+            ctx->st.last_residual = rel;
+            return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "mixed-precision refinement did not converge");
+        }
+        double tol = ctx->opt.mixed_inner_tol;
+        MLPG_TRY(nested_solve<float>(ctx, ctx->res64, ctx->tmp64, nullptr, tol, tol));
+        k_add<double, double><<<nblk(N), kBlock, 0, s>>>(N, ctx->Psi, ctx->tmp64, ctx->Psi);
+        CU_LAUNCH(ctx);
+    }
+    k_Dreduce<double><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, ctx->Psi, ctx->Phi);
+    CU_LAUNCH(ctx);
+    ctx->st.last_refinements = k;
+    ctx->st.last_residual = rel;
+    finish_step_stats(ctx);
+    return MLPG_OK;
+}
+
+}  // namespace mlpg

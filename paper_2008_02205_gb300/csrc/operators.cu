@@ -1,0 +1,550 @@
+// Transport operators of one backward-Euler step (Sec. 4.2) and the batched
+// transport operator apply over all directions.
+//
+// With kappa = 1/(c dt) and tau_i the SUPG length, the direction enters L_m
+// only through Omega^a, Omega^a Omega^b and the outflow selector
+// max(Omega . n_f, 0), so L_m is a combination of direction-independent arrays
+// on one CSR pattern (rows scaled by tau_i where the weak form has tau_i):
+//   A0  = kappa M0 + Mt                         coefficient 1
+//   Aa  = (kappa tau - 1) G^a + tau Gt^a        coefficient Omega^a
+//   Aaa = tau K^aa, Axy = tau (K^xy + K^yx)     coefficients Omega^a Omega^a, Omega^x Omega^y
+//   S_f                                         coefficient max(Omega . n_f, 0)
+//   T_m  = kappa (M0 + tau Omega^a G^a)
+//   MS_m = (Ms + tau Omega^a Gs^a) / (4 pi)
+//   r_m  = Q0 + tau Omega^a Q^a + sum_f max(-Omega . n_f, 0) psi_b,f B_f
+// FP64 path: the values of every L_m are materialised once per dt, [nnz][m]
+// (direction fastest), and one apply is a single multiply-add per entry.
+// FP32 path: the six arrays are streamed once per apply and combined per
+// direction in registers; the face terms live in a separate short segment
+// per boundary row.
+#include <cmath>
+
+#include "internal.h"
+
+namespace mlpg {
+
+namespace {
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+__global__ void k_rowidx(int64_t n, const int32_t *__restrict__ rowptr, int32_t *__restrict__ rowidx) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) rowidx[p] = (int32_t)i;
+}
+
+__global__ void k_form_arrays(int64_t nnz, double kappa, const int32_t *__restrict__ rowidx,
+                              const double *__restrict__ tau, const double *__restrict__ mats,
+                              double *__restrict__ A64, float *__restrict__ A32,
+                              double *__restrict__ T64, double *__restrict__ S64) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= nnz) return;
+    const double t = tau[rowidx[p]];
+    const double *M0 = mats, *Mt = mats + nnz, *Ms = mats + 2 * nnz;
+    const double *Gx = mats + 3 * nnz, *Gy = mats + 4 * nnz, *Gtx = mats + 5 * nnz,
+                 *Gty = mats + 6 * nnz, *Gsx = mats + 7 * nnz, *Gsy = mats + 8 * nnz;
+    const double *Kxx = mats + 9 * nnz, *Kxy = mats + 10 * nnz, *Kyx = mats + 11 * nnz,
+                 *Kyy = mats + 12 * nnz;
+    double a[6];
+    a[0] = kappa * M0[p] + Mt[p];
+    a[1] = (kappa * t - 1.0) * Gx[p] + t * Gtx[p];
+    a[2] = (kappa * t - 1.0) * Gy[p] + t * Gty[p];
+    a[3] = t * Kxx[p];
+    a[4] = t * Kyy[p];
+    a[5] = t * (Kxy[p] + Kyx[p]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        A64[k * nnz + p] = a[k];
+        A32[k * nnz + p] = (float)a[k];
+    }
+    T64[p] = kappa * M0[p];
+    T64[nnz + p] = kappa * t * Gx[p];
+    T64[2 * nnz + p] = kappa * t * Gy[p];
+    S64[p] = Ms[p];
+    S64[nnz + p] = t * Gsx[p];
+    S64[2 * nnz + p] = t * Gsy[p];
+}
+
+__global__ void k_coef(int m, const double *__restrict__ omega, double *__restrict__ coef,
+                       double *__restrict__ fcoef) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    double ox = omega[3 * k], oy = omega[3 * k + 1];
+    double *c = coef + 8 * k;
+    c[0] = 1.0; c[1] = ox; c[2] = oy; c[3] = ox * ox; c[4] = oy * oy; c[5] = ox * oy; c[6] = 0; c[7] = 0;
+    // faces -x, +x, -y, +y: outward normals; outflow coefficient max(Omega . n, 0)
+    fcoef[4 * k + 0] = fmax(-ox, 0.0);
+    fcoef[4 * k + 1] = fmax(ox, 0.0);
+    fcoef[4 * k + 2] = fmax(-oy, 0.0);
+    fcoef[4 * k + 3] = fmax(oy, 0.0);
+}
+
+__global__ void k_materialize(int64_t nnz, int m, const double *__restrict__ A64,
+                              const double *__restrict__ Sf, const double *__restrict__ coef,
+                              const double *__restrict__ fcoef, double *__restrict__ L64) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz * m) return;
+    int64_t p = e / m;
+    int k = (int)(e - p * m);
+    const double *c = coef + 8 * k, *fc = fcoef + 4 * k;
+    double v = A64[p];
+#pragma unroll
+    for (int j = 1; j < 6; ++j) v += c[j] * A64[j * nnz + p];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v += fc[f] * Sf[f * nnz + p];
+    L64[e] = v;
+}
+
+__global__ void k_diag_rhs(int64_t n, int m, const int32_t *__restrict__ diag, int64_t nnz,
+                           const double *__restrict__ A64, const double *__restrict__ Sf,
+                           const double *__restrict__ coef, const double *__restrict__ fcoef,
+                           const double *__restrict__ tau, const double *__restrict__ vecs,
+                           double4 psib, double *__restrict__ dinv64, float *__restrict__ dinv32,
+                           double *__restrict__ r64, int *__restrict__ flag) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    int64_t i = e / m;
+    int k = (int)(e - i * m);
+    const double *c = coef + 8 * k, *fc = fcoef + 4 * k;
+    int32_t p = diag[i];
+    double d = A64[p];
+    for (int j = 1; j < 6; ++j) d += c[j] * A64[j * nnz + p];
+    for (int f = 0; f < 4; ++f) d += fc[f] * Sf[f * nnz + p];
+    if (!(fabs(d) > 0.0)) {
+        atomicOr(flag, 16);
+        d = 1.0;
+    }
+    dinv64[e] = 1.0 / d;
+    dinv32[e] = (float)(1.0 / d);
+    const double *Q0 = vecs, *Qx = vecs + n, *Qy = vecs + 2 * n, *B = vecs + 3 * n;
+    double ox = c[1], oy = c[2];
+    double r = Q0[i] + tau[i] * (ox * Qx[i] + oy * Qy[i]);
+    // inflow faces: Omega . n_f < 0, coefficient |Omega . n_f| = max(-Omega . n_f, 0)
+    double pb[4] = {psib.x, psib.y, psib.z, psib.w};
+    double inc[4] = {fmax(ox, 0.0), fmax(-ox, 0.0), fmax(oy, 0.0), fmax(-oy, 0.0)};
+    for (int f = 0; f < 4; ++f) r += inc[f] * pb[f] * B[f * n + i];
+    r64[e] = r;
+}
+
+// boundary segment: entries of rows that touch a face (S_f != 0)
+__global__ void k_bcount(int64_t n, const int32_t *__restrict__ rowptr, int64_t nnz,
+                         const double *__restrict__ Sf, int *__restrict__ cnt) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = 0;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        bool nz = false;
+        for (int f = 0; f < 4; ++f) nz |= Sf[f * nnz + p] != 0.0;
+        c += nz;
+    }
+    cnt[i] = c;
+}
+
+__global__ void k_bfill(int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                        int64_t nnz, const double *__restrict__ Sf, const int32_t *__restrict__ bptr,
+                        int64_t nb, int32_t *__restrict__ bcol, double *__restrict__ bval64,
+                        float *__restrict__ bval32) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t o = bptr[i];
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        bool nz = false;
+        for (int f = 0; f < 4; ++f) nz |= Sf[f * nnz + p] != 0.0;
+        if (!nz) continue;
+        bcol[o] = col[p];
+        for (int f = 0; f < 4; ++f) {
+            bval64[f * nb + o] = Sf[f * nnz + p];
+            bval32[f * nb + o] = (float)Sf[f * nnz + p];
+        }
+        ++o;
+    }
+}
+
+__global__ void k_scan1(int64_t n, const int *__restrict__ in, int32_t *__restrict__ out) {
+    __shared__ long long part[1024];
+    int t = threadIdx.x, T = blockDim.x;
+    int64_t chunk = (n + T - 1) / T;
+    int64_t a = t * chunk, b = min(n, a + chunk);
+    long long s = 0;
+    for (int64_t k = a; k < b; ++k) s += in[k];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        long long v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    long long run = part[t] - s;
+    for (int64_t k = a; k < b; ++k) {
+        out[k] = (int32_t)run;
+        run += in[k];
+    }
+    if (t == T - 1) out[n] = (int32_t)part[T - 1];
+}
+
+// ---------------------------------------------------------------------------
+// batched L-apply.  A team of TM lanes (power of two) works on one row; lane l
+// owns directions m = l + TM t, t < DPL.  Y = L X, or Y = B - L X when B != 0.
+// ---------------------------------------------------------------------------
+template <int DPL>
+__global__ void __launch_bounds__(256) k_spmm64(int64_t n, int m, int tm_log2,
+                                                const int32_t *__restrict__ rowptr,
+                                                const int32_t *__restrict__ col,
+                                                const double *__restrict__ L64,
+                                                const double *__restrict__ X, const double *__restrict__ B,
+                                                double *__restrict__ Y) {
+    const int TM = 1 << tm_log2;
+    const int lane = threadIdx.x & (TM - 1);
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
+    if (row >= n) return;
+    double acc[DPL];
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) acc[t] = 0.0;
+    const int32_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    for (int32_t p = p0; p < p1; ++p) {
+        const int64_t j = col[p];
+        const double *lv = L64 + (int64_t)p * m;
+        const double *xv = X + j * m;
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) acc[t] = fma(lv[k], xv[k], acc[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) {
+        int k = lane + t * TM;
+        if (k < m) {
+            int64_t e = row * m + k;
+            Y[e] = B ? B[e] - acc[t] : acc[t];
+        }
+    }
+}
+
+template <int DPL>
+__global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, int64_t nnz, int64_t nb,
+                                                const int32_t *__restrict__ rowptr,
+                                                const int32_t *__restrict__ col,
+                                                const float *__restrict__ A32,
+                                                const int32_t *__restrict__ bptr,
+                                                const int32_t *__restrict__ bcol,
+                                                const float *__restrict__ bval,
+                                                const double *__restrict__ coef,
+                                                const double *__restrict__ fcoef,
+                                                const float *__restrict__ X, const float *__restrict__ B,
+                                                float *__restrict__ Y) {
+    const int TM = 1 << tm_log2;
+    const int lane = threadIdx.x & (TM - 1);
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
+    if (row >= n) return;
+    float c1[DPL], c2[DPL], c3[DPL], c4[DPL], c5[DPL], acc[DPL];
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) {
+        int k = lane + t * TM;
+        k = k < m ? k : m - 1;
+        c1[t] = (float)coef[8 * k + 1];
+        c2[t] = (float)coef[8 * k + 2];
+        c3[t] = (float)coef[8 * k + 3];
+        c4[t] = (float)coef[8 * k + 4];
+        c5[t] = (float)coef[8 * k + 5];
+        acc[t] = 0.0f;
+    }
+    const int32_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    for (int32_t p = p0; p < p1; ++p) {
+        const int64_t j = col[p];
+        const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
+                    a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
+        const float *xv = X + j * m;
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) {
+                float v = fmaf(c5[t], a5, fmaf(c4[t], a4, fmaf(c3[t], a3, fmaf(c2[t], a2, fmaf(c1[t], a1, a0)))));
+                acc[t] = fmaf(v, xv[k], acc[t]);
+            }
+        }
+    }
+    const int32_t b0 = bptr[row], b1 = bptr[row + 1];
+    for (int32_t p = b0; p < b1; ++p) {
+        const int64_t j = bcol[p];
+        const float s0 = bval[p], s1 = bval[nb + p], s2 = bval[2 * nb + p], s3 = bval[3 * nb + p];
+        const float *xv = X + j * m;
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) {
+                const double *fc = fcoef + 4 * k;
+                float v = (float)fc[0] * s0 + (float)fc[1] * s1 + (float)fc[2] * s2 + (float)fc[3] * s3;
+                acc[t] = fmaf(v, xv[k], acc[t]);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) {
+        int k = lane + t * TM;
+        if (k < m) {
+            int64_t e = row * m + k;
+            Y[e] = B ? B[e] - acc[t] : acc[t];
+        }
+    }
+}
+
+// RHS f[i][m] = (T_m X)_i + r[i][m] with T_m = T0 + Omega^x Tx + Omega^y Ty (FP64).
+template <int DPL>
+__global__ void __launch_bounds__(256) k_rhs64(int64_t n, int m, int tm_log2, int64_t nnz,
+                                               const int32_t *__restrict__ rowptr,
+                                               const int32_t *__restrict__ col,
+                                               const double *__restrict__ T64,
+                                               const double *__restrict__ coef,
+                                               const double *__restrict__ X, const double *__restrict__ r,
+                                               double *__restrict__ F) {
+    const int TM = 1 << tm_log2;
+    const int lane = threadIdx.x & (TM - 1);
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
+    if (row >= n) return;
+    double acc[DPL], cx[DPL], cy[DPL];
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) {
+        int k = lane + t * TM;
+        k = k < m ? k : m - 1;
+        cx[t] = coef[8 * k + 1];
+        cy[t] = coef[8 * k + 2];
+        acc[t] = 0.0;
+    }
+    for (int32_t p = rowptr[row]; p < rowptr[row + 1]; ++p) {
+        const int64_t j = col[p];
+        const double t0 = T64[p], tx = T64[nnz + p], ty = T64[2 * nnz + p];
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) acc[t] = fma(fma(cy[t], ty, fma(cx[t], tx, t0)), X[j * m + k], acc[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) {
+        int k = lane + t * TM;
+        if (k < m) F[row * m + k] = acc[t] + r[row * m + k];
+    }
+}
+
+// a = Ms Phi, bx = tau Gs^x Phi, by = tau Gs^y Phi (three SpMVs on one vector)
+__global__ void k_ms_spmv(int64_t n, int64_t nnz, const int32_t *__restrict__ rowptr,
+                          const int32_t *__restrict__ col, const double *__restrict__ S64,
+                          const double *__restrict__ phi, double *__restrict__ abc) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = 0, bx = 0, by = 0;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        double v = phi[col[p]];
+        a = fma(S64[p], v, a);
+        bx = fma(S64[nnz + p], v, bx);
+        by = fma(S64[2 * nnz + p], v, by);
+    }
+    abc[i] = a;
+    abc[n + i] = bx;
+    abc[2 * n + i] = by;
+}
+
+template <typename T>
+__global__ void k_ms_expand(int64_t n, int m, const double *__restrict__ abc,
+                            const double *__restrict__ coef, T *__restrict__ out) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    int64_t i = e / m;
+    int k = (int)(e - i * m);
+    double v = (abc[i] + coef[8 * k + 1] * abc[n + i] + coef[8 * k + 2] * abc[2 * n + i]) / kFourPi;
+    out[e] = (T)v;
+}
+
+__global__ void k_interp_apply(int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                               const double *__restrict__ I, const double *__restrict__ phi,
+                               double *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = fma(I[p], phi[col[p]], s);
+    out[i] = s;
+}
+
+struct Team {
+    int tm_log2, dpl;
+};
+Team pick_team(int m) {
+    Team best{5, (m + 31) / 32};
+    double beff = -1.0;
+    for (int lg = 5; lg >= 2; --lg) {
+        int tm = 1 << lg;
+        int dpl = (m + tm - 1) / tm;
+        if (dpl > 16) continue;
+        double eff = double(m) / double(tm * dpl);
+        if (eff > beff + 0.05) { beff = eff; best = {lg, dpl}; }
+    }
+    return best;
+}
+
+}  // namespace
+
+#define DISPATCH_DPL(dpl, KERNEL, ...)                                   \
+    switch (dpl) {                                                       \
+        case 1: KERNEL<1><<<grid, 256, 0, s>>>(__VA_ARGS__); break;      \
+        case 2: KERNEL<2><<<grid, 256, 0, s>>>(__VA_ARGS__); break;      \
+        case 3: KERNEL<3><<<grid, 256, 0, s>>>(__VA_ARGS__); break;      \
+        case 4: KERNEL<4><<<grid, 256, 0, s>>>(__VA_ARGS__); break;      \
+        case 5: case 6: KERNEL<6><<<grid, 256, 0, s>>>(__VA_ARGS__); break; \
+        case 7: case 8: KERNEL<8><<<grid, 256, 0, s>>>(__VA_ARGS__); break; \
+        default: KERNEL<16><<<grid, 256, 0, s>>>(__VA_ARGS__); break;    \
+    }
+
+static int64_t team_grid(int64_t n, const Team &tm) {
+    int64_t threads = n << tm.tm_log2;
+    return (threads + 255) / 256;
+}
+
+static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
+    const int64_t n = ctx->n, nnz = ctx->nnz;
+    const int m = ctx->m;
+    cudaStream_t s = ctx->stream;
+    MLPG_TRY(dalloc(ctx, &ctx->rowidx, nnz));
+    k_rowidx<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, ctx->rowidx);
+    CU_LAUNCH(ctx);
+    MLPG_TRY(dalloc(ctx, &ctx->A64, 6 * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->A32, 6 * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->T64, 3 * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->S64, 3 * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->L64, (size_t)nnz * m));
+    MLPG_TRY(dalloc(ctx, &ctx->coef, 8 * m));
+    MLPG_TRY(dalloc(ctx, &ctx->fcoef, 4 * m));
+    MLPG_TRY(dalloc(ctx, &ctx->dinv64, (size_t)n * m));
+    MLPG_TRY(dalloc(ctx, &ctx->dinv32, (size_t)n * m));
+    MLPG_TRY(dalloc(ctx, &ctx->r64, (size_t)n * m));
+    MLPG_TRY(dalloc(ctx, &ctx->abc, 3 * n));
+    // boundary segment (the face arrays do not depend on dt)
+    int *cnt;
+    MLPG_TRY(dalloc(ctx, &cnt, n));
+    MLPG_TRY(dalloc(ctx, &ctx->bptr, n + 1));
+    const double *Sf = ctx->mats + 13 * nnz;
+    k_bcount<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, nnz, Sf, cnt);
+    CU_LAUNCH(ctx);
+    k_scan1<<<1, 1024, 0, s>>>(n, cnt, ctx->bptr);
+    CU_LAUNCH(ctx);
+    int32_t nb32 = 0;
+    CU(ctx, cudaMemcpyAsync(&nb32, ctx->bptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    ctx->nb = nb32;
+    MLPG_TRY(dalloc(ctx, &ctx->bcol, ctx->nb));
+    MLPG_TRY(dalloc(ctx, &ctx->bval64, 4 * ctx->nb));
+    MLPG_TRY(dalloc(ctx, &ctx->bval32, 4 * ctx->nb));
+    k_bfill<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, ctx->col, nnz, Sf, ctx->bptr, ctx->nb,
+                                            ctx->bcol, ctx->bval64, ctx->bval32);
+    CU_LAUNCH(ctx);
+    k_coef<<<(m + 127) / 128, 128, 0, s>>>(m, ctx->omega, ctx->coef, ctx->fcoef);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
+    const int64_t n = ctx->n, nnz = ctx->nnz;
+    const int m = ctx->m;
+    cudaStream_t s = ctx->stream;
+    if (!ctx->A64) MLPG_TRY(init_operator_storage(ctx));
+    const double *Sf = ctx->mats + 13 * nnz;
+    k_form_arrays<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, kappa, ctx->rowidx, ctx->tau, ctx->mats,
+                                                    ctx->A64, ctx->A32, ctx->T64, ctx->S64);
+    CU_LAUNCH(ctx);
+    int64_t tot = nnz * m;
+    k_materialize<<<(tot + 255) / 256, 256, 0, s>>>(nnz, m, ctx->A64, Sf, ctx->coef, ctx->fcoef, ctx->L64);
+    CU_LAUNCH(ctx);
+    CU(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+    double4 pb = make_double4(ctx->psi_b[0], ctx->psi_b[1], ctx->psi_b[2], ctx->psi_b[3]);
+    int64_t nm = n * m;
+    k_diag_rhs<<<(nm + 255) / 256, 256, 0, s>>>(n, m, ctx->diag, nnz, ctx->A64, Sf, ctx->coef, ctx->fcoef,
+                                                ctx->tau, ctx->vecs, pb, ctx->dinv64, ctx->dinv32, ctx->r64,
+                                                ctx->d_flag);
+    CU_LAUNCH(ctx);
+    int flag = 0;
+    CU(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    if (flag & 16) return set_err(ctx, MLPG_ERR_ARG, "transport operator has a zero diagonal entry");
+    ctx->kappa = kappa;
+    for (int f = 0; f < 6; ++f) ctx->ops_psib[f] = ctx->psi_b[f];
+    ctx->st.spmm_bytes = 0;
+    return MLPG_OK;
+}
+
+// Device time of each batched L-apply: event pairs from a pool, harvested
+// (elapsed time summed) when the pool is full and whenever stats are read.
+static void timing_begin(mlpg_ctx *ctx) {
+    if (!ctx->timing) return;
+    if (ctx->ev_used == (int)ctx->ev_pool.size()) harvest_timing(ctx);
+    cudaEventRecord(ctx->ev_pool[ctx->ev_used].first, ctx->stream);
+}
+static void timing_end(mlpg_ctx *ctx) {
+    ctx->st.spmm_launches++;
+    if (!ctx->timing) return;
+    cudaEventRecord(ctx->ev_pool[ctx->ev_used].second, ctx->stream);
+    ctx->ev_used++;
+}
+
+mlpg_status apply_L64_res(mlpg_ctx *ctx, const double *X, const double *B, double *Y) {
+    Team tm = pick_team(ctx->m);
+    int64_t grid = team_grid(ctx->n, tm);
+    cudaStream_t s = ctx->stream;
+    timing_begin(ctx);
+    DISPATCH_DPL(tm.dpl, k_spmm64, ctx->n, ctx->m, tm.tm_log2, ctx->rowptr, ctx->col, ctx->L64, X, B, Y);
+    timing_end(ctx);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
+    Team tm = pick_team(ctx->m);
+    int64_t grid = team_grid(ctx->n, tm);
+    cudaStream_t s = ctx->stream;
+    timing_begin(ctx);
+    DISPATCH_DPL(tm.dpl, k_spmm32, ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->nb, ctx->rowptr, ctx->col,
+                 ctx->A32, ctx->bptr, ctx->bcol, ctx->bval32, ctx->coef, ctx->fcoef, X, B, Y);
+    timing_end(ctx);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status apply_L64(mlpg_ctx *ctx, const double *X, double *Y) { return apply_L64_res(ctx, X, nullptr, Y); }
+mlpg_status apply_L32(mlpg_ctx *ctx, const float *X, float *Y) { return apply_L32_res(ctx, X, nullptr, Y); }
+
+mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F) {
+    Team tm = pick_team(ctx->m);
+    int64_t grid = team_grid(ctx->n, tm);
+    cudaStream_t s = ctx->stream;
+    DISPATCH_DPL(tm.dpl, k_rhs64, ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->T64,
+                 ctx->coef, Psi_prev, ctx->r64, F);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+template <typename T>
+mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out) {
+    const int64_t n = ctx->n;
+    cudaStream_t s = ctx->stream;
+    k_ms_spmv<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->nnz, ctx->rowptr, ctx->col, ctx->S64, phi, ctx->abc);
+    CU_LAUNCH(ctx);
+    int64_t nm = n * ctx->m;
+    k_ms_expand<T><<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, ctx->abc, ctx->coef, out);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+template mlpg_status apply_MS<double>(mlpg_ctx *, const double *, double *);
+template mlpg_status apply_MS<float>(mlpg_ctx *, const double *, float *);
+
+mlpg_status interp_flux(mlpg_ctx *ctx, double *out_dev, int kind) {
+    const int64_t n = ctx->n;
+    if (kind == 1) {
+        CU(ctx, cudaMemcpyAsync(out_dev, ctx->Phi, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        return MLPG_OK;
+    }
+    k_interp_apply<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->rowptr, ctx->col, ctx->interp, ctx->Phi,
+                                                              out_dev);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+}  // namespace mlpg

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Stage by stage on the same seeded inputs: overlap pattern (bit-exact), cell
+volumes, integrated forms, the batched transport operator, one backward-Euler
+step, whole time-dependent runs in FP64 and mixed precision, the steady
+problem with inflow, a rectangular domain with ragged rows, and the error
+paths.  Tolerances: 1e-9 relative L2 on the scalar flux in FP64 mode, 1e-8 in
+mixed mode (FP32 operator streams, FP64 refinement); forms and volumes to
+rounding (1e-12 of each array's magnitude).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import mlpg_inputs as mi  # noqa: E402
+import oracle.mlpg_oracle as O  # noqa: E402
+import paper_2008_02205_gb300 as pkg  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def small():
+    prob = mi.small_2d(14, sn=4, seed=1001, steps=3)
+    disc = O.Discretization(prob.x, prob.R)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    tp = pkg.TransportProblem.from_problem(prob, inner_tol=1e-13, outer_tol=1e-13)
+    tp.integrate().assemble()
+    yield prob, disc, F, tp
+    tp.close()
+
+
+def test_neighbors_bit_exact(small):
+    prob, disc, F, tp = small
+    rowptr, col = tp.neighbors()
+    assert np.array_equal(rowptr, disc.rowptr)
+    assert np.array_equal(col, disc.col)
+
+
+def test_volumes(small):
+    prob, disc, F, tp = small
+    V = tp.volumes()
+    assert np.abs(V - disc.V).max() <= 1e-15 + 1e-13 * disc.V.max()
+    assert abs(V.sum() - 1.0) < 1e-13
+
+
+def test_forms(small):
+    prob, disc, F, tp = small
+    mats, vecs = tp.forms()
+    d = 2
+    ref_m = np.concatenate([F["M0"][None], F["Mt"][None], F["Ms"][None], F["G"], F["Gt"], F["Gs"],
+                            F["K"].reshape(d * d, -1), F["S"]])
+    ref_v = np.concatenate([F["Q0"][None], F["Q"], F["B"]])
+    assert mats.shape == ref_m.shape and vecs.shape == ref_v.shape
+    for k in range(ref_m.shape[0]):
+        scale = np.abs(ref_m[k]).max()
+        assert np.abs(mats[k] - ref_m[k]).max() <= 1e-12 * scale, k
+    for k in range(ref_v.shape[0]):
+        scale = max(np.abs(ref_v[k]).max(), 1e-300)
+        assert np.abs(vecs[k] - ref_v[k]).max() <= 1e-12 * scale, k
+
+
+@pytest.mark.parametrize("precision,tol", [(pkg.MLPG_FP64, 1e-13), (pkg.MLPG_MIXED, 3e-6)])
+def test_apply_L(small, precision, tol):
+    prob, disc, F, tp = small
+    tr = O.Transport(disc, F, prob.omega, prob.w)
+    rng = np.random.default_rng(7)
+    X = rng.uniform(-1, 1, (prob.n, prob.m))
+    dt = prob.dt
+    dtype = torch.float64 if precision == pkg.MLPG_FP64 else torch.float32
+    Xd = torch.tensor(X, dtype=dtype, device="cuda")
+    Yd = torch.empty_like(Xd)
+    pkg.mlpg_apply_L_dev(tp.ctx, dt, precision, Xd.data_ptr(), Yd.data_ptr())
+    torch.cuda.synchronize()
+    Y = Yd.double().cpu().numpy()
+    ref = np.stack([tr.L_matrix(m, 1.0 / dt) @ X[:, m] for m in range(prob.m)], axis=1)
+    assert _rel(Y, ref) < tol
+
+
+def _oracle_run(prob, steps=None, dt=None, inflow=None):
+    disc = O.Discretization(prob.x, prob.R, prob.lo, prob.hi)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    tr = O.Transport(disc, F, prob.omega, prob.w, psi_b=inflow if inflow is not None else prob.inflow)
+    s = O.Solver(tr, outer_tol=1e-13)
+    Psi, Phi, st = s.run(np.zeros((tr.M, disc.n)), prob.dt if dt is None else dt,
+                         prob.steps if steps is None else steps)
+    return disc.interpolation_matrix() @ Phi, Phi, Psi, st
+
+
+def test_small_run_fp64(small):
+    prob, disc, F, tp = small
+    phi = tp.run(prob.dt, prob.steps)
+    ref, Phi_ref, Psi_ref, _ = _oracle_run(prob)
+    assert _rel(phi, ref) < 1e-9
+    assert _rel(tp.scalar_flux(kind=1), Phi_ref) < 1e-9
+    assert _rel(tp.state(), Psi_ref.T) < 1e-9
+    st = tp.stats()
+    assert st["steps"] == prob.steps and st["last_residual"] < 1e-10
+
+
+def test_config_1024_points_S4_10_steps_fp64():
+    """2D unit square, 32x32 jittered points, S4, sigma_t 1, sigma_s 0.5, q 1,
+    vacuum, dt 0.01 x 10 steps, FP64: scalar flux within 1e-9 of the oracle."""
+    prob = mi.small_2d(32, sn=4, seed=1000, steps=10, dt=0.01)
+    ref, *_ = _oracle_run(prob)
+    with pkg.TransportProblem.from_problem(prob, inner_tol=1e-13, outer_tol=1e-13) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+    assert _rel(phi, ref) < 1e-9
+
+
+def test_config_1024_points_mixed():
+    prob = mi.small_2d(32, sn=4, seed=1000, steps=10, dt=0.01)
+    ref, *_ = _oracle_run(prob)
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, refine_tol=1e-12) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+        st = tp.stats()
+    assert _rel(phi, ref) < 1e-8
+    assert st["last_refinements"] >= 1
+
+
+def test_steady_with_inflow_and_two_region():
+    prob = mi.two_region_2d(n_per_dim=16, sn=4, seed=2001, steps=1)
+    inflow = {0: 1.0, 3: 0.5}
+    ref, *_ = _oracle_run(prob, steps=1, dt=np.inf, inflow=inflow)
+    with pkg.TransportProblem(prob.x, prob.R, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q,
+                              inflow=inflow, inner_tol=1e-13, outer_tol=1e-13) as tp:
+        tp.integrate().assemble()
+        tp.step(math.inf)
+        phi = tp.scalar_flux()
+    assert _rel(phi, ref) < 1e-9
+
+
+def test_rectangle_ragged_rows():
+    # 17 x 11 jittered points on [0, 1.7] x [0, 1.1]: ragged rows, non-unit box
+    rng = np.random.default_rng(5)
+    h = 0.1
+    gx, gy = np.meshgrid((np.arange(17) + 0.5) * h, (np.arange(11) + 0.5) * h)
+    x = np.stack([gx.ravel(), gy.ravel()], 1) + h * rng.uniform(-0.2, 0.2, (187, 2))
+    om, w = mi.level_symmetric(6, 2)
+    n = len(x)
+    prob = mi.Problem("rect", 2, x, np.full(n, 2 * h), om, w, np.full(n, 2.0), np.full(n, 1.5),
+                      rng.uniform(0, 1, n), dt=0.05, steps=2, lo=(0, 0, 0), hi=(1.7, 1.1, 1))
+    ref, *_ = _oracle_run(prob)
+    with pkg.TransportProblem.from_problem(prob, lo=(0, 0, 0), hi=(1.7, 1.1, 1), inner_tol=1e-13,
+                                           outer_tol=1e-13) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+    assert _rel(phi, ref) < 1e-9
+
+
+def test_initial_state_and_restart(small):
+    prob, disc, F, _ = small
+    rng = np.random.default_rng(3)
+    psi0 = rng.uniform(0, 0.1, (prob.n, prob.m))
+    # run 2 steps in one go vs 1 step, save, new context, restore, 1 step
+    with pkg.TransportProblem.from_problem(prob, inner_tol=1e-13, outer_tol=1e-13) as a:
+        a.integrate().assemble()
+        a.set_state(psi0)
+        phi2 = a.run(prob.dt, 2)
+    with pkg.TransportProblem.from_problem(prob, inner_tol=1e-13, outer_tol=1e-13) as b:
+        b.integrate().assemble()
+        b.set_state(psi0)
+        b.step(prob.dt)
+        saved = b.state()
+    with pkg.TransportProblem.from_problem(prob, inner_tol=1e-13, outer_tol=1e-13) as c:
+        c.integrate().assemble()
+        c.set_state(saved)
+        phi2b = c.run(prob.dt, 1)
+    assert _rel(phi2b, phi2) < 1e-11
+
+
+def test_error_paths():
+    prob = mi.small_2d(8, sn=2, steps=1)
+    # out of order
+    tp = pkg.TransportProblem.from_problem(prob)
+    with pytest.raises(pkg.MlpgError) as e:
+        tp.step(0.1)
+    assert e.value.status == -2
+    tp.integrate()
+    with pytest.raises(pkg.MlpgError) as e:
+        tp.integrate()
+    assert e.value.status == -2
+    tp.assemble()
+    with pytest.raises(pkg.MlpgError) as e:
+        tp.step(-1.0)
+    assert e.value.status == -1
+    tp.close()
+    # point outside the box
+    x = prob.x.copy()
+    x[0, 0] = 1.5
+    with pytest.raises(pkg.MlpgError) as e:
+        pkg.TransportProblem(x, prob.R, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q)
+    assert e.value.status == -5
+    # kernels too small to span a linear basis: singular RK moment matrix
+    with pytest.raises(pkg.MlpgError) as e:
+        t2 = pkg.TransportProblem(prob.x, 0.45 * prob.R, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q)
+        t2.integrate()
+    assert e.value.status == -6
+    # iteration cap
+    with pkg.TransportProblem.from_problem(prob, max_inner=1, inner_restart=2) as t3:
+        t3.integrate().assemble()
+        with pytest.raises(pkg.MlpgError) as e:
+            t3.step(0.01)
+        assert e.value.status == -7
