@@ -1,0 +1,311 @@
+"""Benchmark: time-dependent discrete-ordinates solves per second on one GB300.
+
+One bench step is one whole solve of the two-region problem through the C ABI:
+create (inputs already in HBM) -> integrate (neighbours, cells, quadrature,
+RK interpolation) -> assemble (all forms) -> 20 backward-Euler steps (nested
+GMRES, mixed precision with FP64 refinement by default) -> scalar flux.
+
+Workload: 2D unit square, 256x256 jittered points (support 2h, linear RK),
+level-symmetric S8 (40 directions), sigma_t = 100 in [0.4,0.6]^2 and 1
+elsewhere, sigma_s = 0.9 sigma_t, q = 1 for x < 0.5, vacuum boundaries,
+dt = 0.005, 20 steps.  Synthetic, seeded inputs (numpy PCG64).
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead, on a
+bounded sample of the same workload (see `_reference`).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "2d-two-region-256x256-S8-20steps"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--n", type=int, default=256, help="points per side (default: the 256x256 workload)")
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end solves")
+    ap.add_argument("--be-steps", type=int, default=None,
+                    help="backward-Euler steps per solve (default: the workload's 20; profiling runs use fewer)")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = []
+        reasons = set()
+        smax = None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+SAMPLE_SIDE = 48
+
+
+def _oracle_sample(reps=1):
+    """CPU oracle on a bounded sample of the workload: the same two-region S8
+    recipe at 48x48 points (about 28x fewer unknowns), one whole 20-step solve,
+    as it stands (exact sparse-LU inner solves, unpreconditioned outer GMRES).
+    solves/s is scaled to the 256x256 workload by the ratio of unknowns."""
+    import oracle.mlpg_oracle as O
+    import mlpg_inputs as mi
+    prob = mi.two_region_2d(n_per_dim=SAMPLE_SIDE)
+    times = []
+    for _ in range(max(reps, 1)):
+        t0 = time.perf_counter()
+        O.solve_problem(prob, outer_tol=1e-12)
+        times.append(time.perf_counter() - t0)
+    scale = (SAMPLE_SIDE * SAMPLE_SIDE) / (256 * 256)
+    sample_s = statistics.median(times)
+    value = scale / sample_s
+    cores = 1
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        cores = max([i.get("num_threads", 1) or 1 for i in info] + [1])
+    except Exception:
+        pass
+    return {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{SAMPLE_SIDE}x{SAMPLE_SIDE} points, same recipe, full 20-step solve, "
+                      f"{sample_s:.2f} s each; scaled by unknowns {SAMPLE_SIDE**2}/65536"}
+
+
+def _reference(args):
+    cb = _oracle_sample(args.steps)
+    value = cb["value"]
+    line = {"metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": 0, "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": f"{SAMPLE_SIDE}x{SAMPLE_SIDE}"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = _args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        if rank == 0:
+            _reference(args)
+        return
+    import torch
+    import mlpg_inputs as mi
+    import paper_2008_02205_gb300 as pkg
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    # independent problems per rank (weak scaling): seed by rank
+    prob = mi.two_region_2d(n_per_dim=args.n, seed=2000 + rank)
+    if args.be_steps is not None:
+        prob.steps = args.be_steps
+    prec = pkg.MLPG_MIXED if args.precision == "mixed" else pkg.MLPG_FP64
+    stream = torch.cuda.current_stream(dev)
+    opts = dict(precision=prec, stream=stream.cuda_stream)
+    host = dict(x=prob.x, R=prob.R, om=prob.omega, w=prob.w, st=prob.sigma_t, ss=prob.sigma_s, q=prob.q)
+    dv = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in host.items()}
+    flux = torch.empty(prob.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    def solve_device(timing=False):
+        o = pkg.mlpg_default_options(**opts)
+        ctx = pkg.mlpg_create_dev(o, prob.n, prob.m, dv["x"].data_ptr(), dv["R"].data_ptr(), dv["om"].data_ptr(),
+                                  dv["w"].data_ptr(), dv["st"].data_ptr(), dv["ss"].data_ptr(), dv["q"].data_ptr())
+        try:
+            if timing:
+                pkg.mlpg_enable_timing(ctx, True)
+            pkg.mlpg_integrate(ctx)
+            pkg.mlpg_assemble(ctx)
+            for _ in range(prob.steps):
+                pkg.mlpg_step(ctx, prob.dt)
+            pkg.mlpg_scalar_flux_dev(ctx, flux.data_ptr(), 0)
+            return pkg.mlpg_get_stats(ctx)
+        finally:
+            pkg.mlpg_destroy(ctx)
+
+    def solve_host():
+        o = pkg.mlpg_default_options(**opts)
+        ctx = pkg.mlpg_create(o, host["x"], host["R"], host["om"], host["w"], host["st"], host["ss"], host["q"])
+        try:
+            pkg.mlpg_integrate(ctx)
+            pkg.mlpg_assemble(ctx)
+            for _ in range(prob.steps):
+                pkg.mlpg_step(ctx, prob.dt)
+            return pkg.mlpg_scalar_flux(ctx, prob.n, 0)
+        finally:
+            pkg.mlpg_destroy(ctx)
+
+    for _ in range(args.warmup):
+        solve_device()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    per = []
+    stats = None
+    spmm_ms, spmm_launch, launches = 0.0, 0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = solve_device(timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per.append(e0.elapsed_time(e1))
+        spmm_ms += stats["spmm_ms"]
+        spmm_launch += stats["spmm_launches"]
+        launches += stats["kernel_launches"]
+    clk = clocks.stop()
+    tot_ms = sum(per)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps / (tot_ms / 1e3)
+    # end to end through the host-pointer API (copies inside the timed region)
+    e2e_times = []
+    for _ in range(0 if args.no_e2e else max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi_host = solve_host()
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = sum(v.nbytes for v in host.values())
+    e2e_value = world / statistics.mean(e2e_times) if e2e_times else None
+    # FP64 comparison solve (the plain FP64 GPU path) and error of this precision vs it
+    fp64_info = None
+    if not args.no_fp64_compare and prec == pkg.MLPG_MIXED:
+        o = dict(opts)
+        o["precision"] = pkg.MLPG_FP64
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with pkg.TransportProblem.from_problem(prob, **o) as tp:
+            tp.integrate().assemble()
+            phi64 = tp.run(prob.dt, prob.steps)
+        t64 = time.perf_counter() - t0
+        phi_mixed = phi_host if e2e_times else flux.cpu().numpy()
+        err = float(np.linalg.norm(phi_mixed - phi64) / np.linalg.norm(phi64))
+        fp64_info = {"solves_per_s": 1.0 / t64, "rel_l2_vs_fp64": err}
+    hbm, peak_kind = _peaks()
+    roof = None
+    if spmm_launch > 0 and spmm_ms > 0:
+        per_launch_s = spmm_ms / spmm_launch / 1e3
+        achieved = stats["spmm_bytes"] / per_launch_s / 1e9
+        roof = {"kernel": "k_spmm32 (batched L-apply)" if prec == pkg.MLPG_MIXED else "k_spmm64 (batched L-apply)",
+                "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": stats["spmm_bytes"],
+                "us_per_launch": per_launch_s * 1e6}
+    lat = sorted(per)
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+    line = {"metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if prec == pkg.MLPG_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": prob.n, "directions": prob.m, "be_steps": prob.steps,
+                       "precision": args.precision, "l2": "flushed (256 MB write) between timed solves",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": p50, "p99": p99},
+            "iterations": {"outer_last_step": stats["last_outer_iters"],
+                           "inner_last_step": stats["last_inner_iters"],
+                           "inner_solves_last_step": stats["last_inner_solves"],
+                           "refinements_last_step": stats["last_refinements"],
+                           "outer_total": stats["total_outer_iters"], "inner_total": stats["total_inner_iters"]},
+            "fp64_path": fp64_info,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(prob.n * 8)},
+            "roofline": roof, "clocks": clk, "gpu_launches": launches,
+            "cpu_baseline": _oracle_sample(1) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -78,6 +78,7 @@ typedef struct {
     int64_t spmm_launches;       /* batched L-apply launches since create */
     double spmm_ms;              /* their device time (when timing is enabled), ms */
     int64_t spmm_bytes;          /* algorithmic bytes of one batched L-apply (active precision) */
+    int64_t kernel_launches;     /* kernels this context launched since create */
 } mlpg_stats;
 
 /* Default options (values listed in mlpg_options). */

@@ -270,6 +270,7 @@ mlpg_status mlpg_integrate(mlpg_ctx *ctx) {
         CU(ctx, cudaMemcpyAsync(ctx->labels, cells.labels.data(), ctx->nverts * sizeof(int32_t), cudaMemcpyHostToDevice, s));
         CU(ctx, cudaMemcpyAsync(ctx->V, cells.volume.data(), ctx->n * sizeof(double), cudaMemcpyHostToDevice, s));
         MLPG_TRY(run_interp(ctx));  // synchronises
+        MLPG_TRY(build_blocks(ctx));
         ctx->st.nnz = ctx->nnz;
         ctx->st.n_volume_qp = ctx->nvq;
         ctx->st.n_boundary_qp = ctx->nbq;

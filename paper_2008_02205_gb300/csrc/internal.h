@@ -13,6 +13,7 @@
 #define MLPG_MAX_DIR 1024   // directions per problem (one thread per direction in a block row)
 #define MLPG_MAX_RESTART 64 // inner / outer restart length cap for the device Hessenberg arrays
 #define MLPG_MAX_CELL_FUNCS 40  // functions whose support can reach one 2D cell
+#define MLPG_BLOCK_PTS 16       // points per block of the block-Jacobi preconditioner
 
 namespace mlpg {
 
@@ -29,7 +30,11 @@ mlpg_status cuda_fail(mlpg_ctx *ctx, cudaError_t e, const char *what, const char
         cudaError_t _e = (expr);                                                    \
         if (_e != cudaSuccess) return mlpg::cuda_fail((ctx), _e, #expr, __FILE__, __LINE__); \
     } while (0)
-#define CU_LAUNCH(ctx) CU(ctx, cudaGetLastError())
+#define CU_LAUNCH(ctx)               \
+    do {                             \
+        (ctx)->st.kernel_launches++; \
+        CU(ctx, cudaGetLastError()); \
+    } while (0)
 
 // host geometry (geometry.cpp) ----------------------------------------------
 struct HostCells {
@@ -64,6 +69,7 @@ struct Gmres {
     double *h2 = nullptr;  // (R + 1) * M
     double *y = nullptr;   // R * M
     double *bnorm = nullptr, *beta = nullptr, *resid = nullptr;  // M
+    double *nrm2 = nullptr;  // M: squared norms of the current vector
     int *active = nullptr; // M: 1 while iterating in this cycle
     int *kcol = nullptr;   // M: Arnoldi columns used in this cycle
     int *its = nullptr;    // M: total iterations
@@ -145,6 +151,12 @@ struct mlpg_ctx {
     double ops_psib[6] = {0, 0, 0, 0, 0, 0};  // inflow the operators were formed with
     int32_t *rowidx = nullptr;  // [nnz] row of each pattern entry
     double *abc = nullptr;      // [3][n] MS partial products
+
+    // block-Jacobi preconditioner: Morton-ordered blocks of kBlockPts points
+    int64_t nblk = 0;
+    int32_t *bmember = nullptr; // [nblk * kBlockPts] point of each block slot (-1: empty)
+    int32_t *bof = nullptr;     // [n] block * kBlockPts + slot of each point
+    float *Pinv = nullptr;      // [nblk][kBlockPts][kBlockPts][m] inverse diagonal blocks of L_m
     double cur_inner_tol = 0.0; // tolerance of the inner solves inside the outer operator
 
     // stats
@@ -185,5 +197,8 @@ mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F);
 template <typename T>
 mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out);
 mlpg_status interp_flux(mlpg_ctx *ctx, double *out_dev, int kind);
+template <typename T>
+mlpg_status apply_prec(mlpg_ctx *ctx, const T *v, T *z);
+mlpg_status build_blocks(mlpg_ctx *ctx);
 void harvest_timing(mlpg_ctx *ctx);
 }  // namespace mlpg

@@ -23,6 +23,13 @@ namespace mlpg {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kChunkRows = 8;   // FP32 partial sums over this many rows before the FP64 accumulator
+
+// arithmetic type of the element-wise work: FP32 vectors are combined in FP32
+template <typename T>
+struct Arith { using type = double; };
+template <>
+struct Arith<float> { using type = float; };
 
 struct Map2 {       // (direction, row) mapping of a 256-thread block
     int MB, RB, mchunks;
@@ -36,7 +43,7 @@ Map2 map2(int M) {
 }
 int grid_rows(int64_t n, const Map2 &mp, int nl) {
     int64_t maxg = (n + mp.RB - 1) / mp.RB;
-    int64_t g = (1216 + mp.mchunks * nl - 1) / (mp.mchunks * nl);
+    int64_t g = (2 * 152 + mp.mchunks * nl - 1) / (mp.mchunks * nl);
     if (g > maxg) g = maxg;
     if (g < 1) g = 1;
     return (int)g;
@@ -44,17 +51,24 @@ int grid_rows(int64_t n, const Map2 &mp, int nl) {
 
 // partial[(l * G + block) * M + m] = sum over this block's rows of V_l[i][m] * w[i][m]
 template <typename T>
-__global__ void k_dots(int64_t n, int M, int MB, int RB, const T *__restrict__ V, int64_t vstride,
-                       const T *__restrict__ w, double *__restrict__ partial) {
-    extern __shared__ double sh[];
+__global__ void __launch_bounds__(kBlock) k_dots(int64_t n, int M, int MB, int RB, const T *__restrict__ V,
+                                                 int64_t vstride, const T *__restrict__ w,
+                                                 double *__restrict__ partial) {
+    using A = typename Arith<T>::type;
+    __shared__ double sh[kBlock];
     const int t = threadIdx.x, ml = t % MB, r = t / MB;
     const int m = blockIdx.y * MB + ml, l = blockIdx.z, G = gridDim.x;
     double acc = 0.0;
     if (r < RB && m < M) {
         const T *v = V + l * vstride;
-        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += (int64_t)G * RB) {
-            int64_t e = i * M + m;
-            acc += (double)v[e] * (double)w[e];
+        const int64_t stride = (int64_t)G * RB;
+        int64_t i = blockIdx.x * (int64_t)RB + r;
+        while (i < n) {
+            A part = 0;
+#pragma unroll
+            for (int c = 0; c < kChunkRows; ++c, i += stride)
+                if (i < n) part += (A)v[i * M + m] * (A)w[i * M + m];
+            acc += (double)part;
         }
     }
     sh[t] = acc;
@@ -66,45 +80,59 @@ __global__ void k_dots(int64_t n, int M, int MB, int RB, const T *__restrict__ V
     }
 }
 
-// out[l][m] = sum_g partial[l][g][m]   (fixed order: deterministic)
+// out[l * M + m] = sum_g partial[(l * G + g) * M + m]; one warp per output,
+// fixed lane order and shuffle tree: deterministic.
 __global__ void k_reduce(int M, int nl, int G, const double *__restrict__ partial, double *__restrict__ out) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= M * nl) return;
-    int l = e / M, m = e - l * M;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= (int64_t)M * nl) return;
+    const int l = (int)(wid / M), m = (int)(wid - (int64_t)l * M);
     double s = 0.0;
-    for (int g = 0; g < G; ++g) s += partial[((int64_t)l * G + g) * M + m];
-    out[e] = s;
+    for (int g = lane; g < G; g += 32) s += partial[((int64_t)l * G + g) * M + m];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[wid] = s;
 }
 
 // w[i][m] -= sum_{l < nl} h[l][m] V_l[i][m]
 template <typename T>
 __global__ void k_update(int64_t n, int M, int nl, const T *__restrict__ V, int64_t vstride,
                          const double *__restrict__ h, T *__restrict__ w) {
+    using A = typename Arith<T>::type;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * M) return;
     int m = (int)(e % M);
-    double s = (double)w[e];
-    for (int l = 0; l < nl; ++l) s -= h[l * M + m] * (double)V[l * vstride + e];
+    A s = (A)w[e];
+    for (int l = 0; l < nl; ++l) s -= (A)h[l * M + m] * (A)V[l * vstride + e];
     w[e] = (T)s;
 }
 
 // as k_update, and partial sums of the squared result (norm)
 template <typename T>
-__global__ void k_update_norm(int64_t n, int M, int MB, int RB, int nl, const T *__restrict__ V,
-                              int64_t vstride, const double *__restrict__ h, T *__restrict__ w,
-                              double *__restrict__ partial) {
-    extern __shared__ double sh[];
+__global__ void __launch_bounds__(kBlock) k_update_norm(int64_t n, int M, int MB, int RB, int nl,
+                                                        const T *__restrict__ V, int64_t vstride,
+                                                        const double *__restrict__ h, T *__restrict__ w,
+                                                        double *__restrict__ partial) {
+    using A = typename Arith<T>::type;
+    __shared__ double sh[kBlock];
     const int t = threadIdx.x, ml = t % MB, r = t / MB;
     const int m = blockIdx.y * MB + ml, G = gridDim.x;
     double acc = 0.0;
     if (r < RB && m < M) {
-        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += (int64_t)G * RB) {
-            int64_t e = i * M + m;
-            double s = (double)w[e];
-            for (int l = 0; l < nl; ++l) s -= h[l * M + m] * (double)V[l * vstride + e];
-            T st = (T)s;
-            w[e] = st;
-            acc += (double)st * (double)st;
+        const int64_t stride = (int64_t)G * RB;
+        int64_t i = blockIdx.x * (int64_t)RB + r;
+        while (i < n) {
+            A part = 0;
+#pragma unroll 1
+            for (int c = 0; c < kChunkRows; ++c, i += stride) {
+                if (i >= n) break;
+                int64_t e = i * M + m;
+                A s = (A)w[e];
+                for (int l = 0; l < nl; ++l) s -= (A)h[l * M + m] * (A)V[l * vstride + e];
+                T st = (T)s;
+                w[e] = st;
+                part += (A)st * (A)st;
+            }
+            acc += (double)part;
         }
     }
     sh[t] = acc;
@@ -116,16 +144,14 @@ __global__ void k_update_norm(int64_t n, int M, int MB, int RB, int nl, const T 
     }
 }
 
-// Start of a cycle: beta = ||r|| from partials; decide which systems iterate.
-__global__ void k_start(int M, int G, int R, const double *__restrict__ partial, double *__restrict__ bnorm,
+// Start of a cycle: beta = ||r|| (nrm2 = ||r||^2); decide which systems iterate.
+__global__ void k_start(int M, int R, const double *__restrict__ nrm2, double *__restrict__ bnorm,
                         double *__restrict__ g, double *__restrict__ sc, int *__restrict__ active,
                         int *__restrict__ kcol, double *__restrict__ resid, double tol, int set_bnorm,
                         int *__restrict__ count) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
-    double s = 0.0;
-    for (int k = 0; k < G; ++k) s += partial[(int64_t)k * M + m];
-    double beta = sqrt(s);
+    double beta = sqrt(nrm2[m]);
     if (set_bnorm) bnorm[m] = beta;
     resid[m] = beta;
     kcol[m] = 0;
@@ -138,21 +164,19 @@ __global__ void k_start(int M, int G, int R, const double *__restrict__ partial,
 }
 
 // Column j of the Hessenberg matrix, Givens rotations, residual estimate.
-__global__ void k_givens(int M, int G, int R, int j, const double *__restrict__ h1,
-                         const double *__restrict__ h2, const double *__restrict__ partial,
-                         double *__restrict__ H, double *__restrict__ cs, double *__restrict__ sn,
-                         double *__restrict__ g, double *__restrict__ sc, int *__restrict__ active,
-                         int *__restrict__ kcol, int *__restrict__ its, double *__restrict__ resid,
-                         const double *__restrict__ bnorm, double tol, int *__restrict__ count) {
+__global__ void k_givens(int M, int R, int j, const double *__restrict__ h1, const double *__restrict__ h2,
+                         const double *__restrict__ nrm2, double *__restrict__ H, double *__restrict__ cs,
+                         double *__restrict__ sn, double *__restrict__ g, double *__restrict__ sc,
+                         int *__restrict__ active, int *__restrict__ kcol, int *__restrict__ its,
+                         double *__restrict__ resid, const double *__restrict__ bnorm, double tol,
+                         int *__restrict__ count) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     if (!active[m]) {
         sc[m] = 0.0;
         return;
     }
-    double s = 0.0;
-    for (int k = 0; k < G; ++k) s += partial[(int64_t)k * M + m];
-    double hn = sqrt(s);
+    double hn = sqrt(nrm2[m]);
     double *Hm = H + (int64_t)m * (R + 1) * R;  // Hm[row * R + col]
     for (int l = 0; l <= j; ++l) Hm[l * R + j] = h1[l * M + m] + h2[l * M + m];
     Hm[(j + 1) * R + j] = hn;
@@ -186,16 +210,13 @@ __global__ void k_givens(int M, int G, int R, int j, const double *__restrict__ 
     }
 }
 
-// v = w * sc[m]; z = v * dinv (or v)
+// w = w * sc[m]
 template <typename T>
-__global__ void k_scale(int64_t n, int M, T *__restrict__ w, const double *__restrict__ sc,
-                        const T *__restrict__ dinv, T *__restrict__ z) {
+__global__ void k_scale(int64_t n, int M, T *__restrict__ w, const double *__restrict__ sc) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * M) return;
     int m = (int)(e % M);
-    double v = (double)w[e] * sc[m];
-    w[e] = (T)v;
-    z[e] = dinv ? (T)(v * (double)dinv[e]) : (T)v;
+    w[e] = (T)((double)w[e] * sc[m]);
 }
 
 // y = R^{-1} g per system (upper triangular part of the rotated Hessenberg)
@@ -212,20 +233,24 @@ __global__ void k_backsolve(int M, int R, const double *__restrict__ H, const do
     }
 }
 
-// x += dinv * sum_{l < kcol[m]} y_l V_l
+// u = sum_{l < kcol[m]} y_l V_l
 template <typename T>
-__global__ void k_xupdate(int64_t n, int M, int kmax, const T *__restrict__ V, int64_t vstride,
-                          const double *__restrict__ y, const int *__restrict__ kcol,
-                          const T *__restrict__ dinv, T *__restrict__ x) {
+__global__ void k_combine(int64_t n, int M, int kmax, const T *__restrict__ V, int64_t vstride,
+                          const double *__restrict__ y, const int *__restrict__ kcol, T *__restrict__ u) {
+    using A = typename Arith<T>::type;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * M) return;
     int m = (int)(e % M);
-    int k = kcol[m];
-    if (k == 0) return;
-    double s = 0.0;
-    for (int l = 0; l < kmax && l < k; ++l) s += y[l * M + m] * (double)V[l * vstride + e];
-    if (dinv) s *= (double)dinv[e];
-    x[e] = (T)((double)x[e] + s);
+    int k = min(kcol[m], kmax);
+    A s = 0;
+    for (int l = 0; l < k; ++l) s += (A)y[l * M + m] * (A)V[l * vstride + e];
+    u[e] = (T)s;
+}
+
+template <typename T>
+__global__ void k_axpy1(int64_t N, const T *__restrict__ u, T *__restrict__ x) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < N) x[e] += u[e];
 }
 
 // out[i] = sum_m w[m] x[i][m]  (angular reduction D, Sec. 4.2)
@@ -301,12 +326,14 @@ static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int
     MLPG_TRY(dalloc(ctx, &G.h2, (size_t)(R + 1) * M));
     MLPG_TRY(dalloc(ctx, &G.y, (size_t)R * M));
     MLPG_TRY(dalloc(ctx, &G.bnorm, M));
+    MLPG_TRY(dalloc(ctx, &G.nrm2, M));
     MLPG_TRY(dalloc(ctx, &G.beta, M));   // scale factors 1/||w||
     MLPG_TRY(dalloc(ctx, &G.resid, M));
     MLPG_TRY(dalloc(ctx, &G.active, M));
     MLPG_TRY(dalloc(ctx, &G.kcol, M));
     MLPG_TRY(dalloc(ctx, &G.its, M));
-    G.partial_cap = (int64_t)1300 * M;
+    // k_dots writes G * nl * M partials with G = ceil(304 / (mchunks nl)) <= 304 / mchunks + 1
+    G.partial_cap = (int64_t)(2 * 152 + MLPG_MAX_RESTART + 8) * M;
     MLPG_TRY(dalloc(ctx, &G.partial, G.partial_cap));
     MLPG_TRY(dalloc(ctx, &G.d_active_count, 1));
     void *hp = nullptr;
@@ -318,39 +345,48 @@ static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int
 
 template <typename T>
 using ApplyFn = std::function<mlpg_status(const T *X, const T *B, T *Y)>;
-
-// Solve A x = b for all M systems; x holds the initial guess.  Returns the
-// summed iteration count in *iters and MLPG_ERR_NOT_CONVERGED on the cap.
 template <typename T>
-static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, const T *dinv, const T *b,
+using PrecFn = std::function<mlpg_status(const T *v, T *z)>;
+
+// Solve A x = b for all M systems, right preconditioned by P (identity when
+// empty); x holds the initial guess.  Returns the summed iteration count in
+// *iters and MLPG_ERR_NOT_CONVERGED on the cap.
+template <typename T>
+static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, const PrecFn<T> &P, const T *b,
                                T *x, double tol, int max_its, int check_every, int64_t *iters) {
     const int64_t n = G.n, N = n * G.M;
     const int M = G.M, R = G.R;
     const int64_t vs = N;
     cudaStream_t s = ctx->stream;
     const Map2 mp = map2(M);
+    const int wblk = (int)((M * 32 + kBlock - 1) / kBlock);
     CU(ctx, cudaMemsetAsync(G.its, 0, sizeof(int) * M, s));
+    auto norm2 = [&](const T *v) -> mlpg_status {   // G.nrm2[m] = ||v_m||^2
+        int g1 = grid_rows(n, mp, 1);
+        k_dots<T><<<dim3(g1, mp.mchunks, 1), kBlock, 0, s>>>(n, M, mp.MB, mp.RB, v, 0, v, G.partial);
+        CU_LAUNCH(ctx);
+        k_reduce<<<wblk, kBlock, 0, s>>>(M, 1, g1, G.partial, G.nrm2);
+        CU_LAUNCH(ctx);
+        return MLPG_OK;
+    };
+    auto precond = [&](const T *v, T *z) -> const T * {
+        if (!P) return v;
+        return P(v, z) == MLPG_OK ? z : nullptr;
+    };
     int64_t total = 0;
     for (int cycle = 0;; ++cycle) {
-        // r = b - A x  -> V_0
-        MLPG_TRY(A(x, b, G.V));
-        int g1 = grid_rows(n, mp, 1);
         if (cycle == 0) {
-            // ||b|| first (into bnorm via k_start with set_bnorm)
-            k_dots<T><<<dim3(g1, mp.mchunks, 1), kBlock, kBlock * sizeof(double), s>>>(n, M, mp.MB, mp.RB, b, 0, b,
-                                                                                     G.partial);
-            CU_LAUNCH(ctx);
+            MLPG_TRY(norm2(b));
             CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
-            k_start<<<(M + 127) / 128, 128, 0, s>>>(M, g1, R, G.partial, G.bnorm, G.g, G.beta, G.active, G.kcol,
-                                                    G.resid, 0.0, 1, G.d_active_count);
+            k_start<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.nrm2, G.bnorm, G.g, G.beta, G.active, G.kcol, G.resid,
+                                                    0.0, 1, G.d_active_count);
             CU_LAUNCH(ctx);
         }
-        k_dots<T><<<dim3(g1, mp.mchunks, 1), kBlock, kBlock * sizeof(double), s>>>(n, M, mp.MB, mp.RB, G.V, 0, G.V,
-                                                                                 G.partial);
-        CU_LAUNCH(ctx);
+        MLPG_TRY(A(x, b, G.V));  // r = b - A x -> V_0
+        MLPG_TRY(norm2(G.V));
         CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
-        k_start<<<(M + 127) / 128, 128, 0, s>>>(M, g1, R, G.partial, G.bnorm, G.g, G.beta, G.active, G.kcol,
-                                                G.resid, tol, 0, G.d_active_count);
+        k_start<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.nrm2, G.bnorm, G.g, G.beta, G.active, G.kcol, G.resid, tol,
+                                                0, G.d_active_count);
         CU_LAUNCH(ctx);
         CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
@@ -359,47 +395,61 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
             *iters = total;
             return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
         }
-        k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, G.V, G.beta, dinv, G.Z);
+        k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, G.V, G.beta);
         CU_LAUNCH(ctx);
+        const T *z = precond(G.V, G.Z);
+        if (!z) return MLPG_ERR_CUDA;
         int jlast = 0;
         for (int j = 0; j < R; ++j) {
             T *w = G.V + (j + 1) * vs;
-            MLPG_TRY(A(G.Z, nullptr, w));
+            MLPG_TRY(A(z, nullptr, w));
             for (int pass = 0; pass < 2; ++pass) {
                 double *hh = pass == 0 ? G.h : G.h2;
                 int gd = grid_rows(n, mp, j + 1);
-                k_dots<T><<<dim3(gd, mp.mchunks, j + 1), kBlock, kBlock * sizeof(double), s>>>(
-                    n, M, mp.MB, mp.RB, G.V, vs, w, G.partial);
+                if ((int64_t)gd * (j + 1) * mp.mchunks * mp.MB > G.partial_cap)
+                    return set_err(ctx, MLPG_ERR_ARG, "reduction buffer too small");
+                k_dots<T><<<dim3(gd, mp.mchunks, j + 1), kBlock, 0, s>>>(n, M, mp.MB, mp.RB, G.V, vs, w, G.partial);
                 CU_LAUNCH(ctx);
-                k_reduce<<<((j + 1) * M + 127) / 128, 128, 0, s>>>(M, j + 1, gd, G.partial, hh);
+                k_reduce<<<(int)(((int64_t)(j + 1) * M * 32 + kBlock - 1) / kBlock), kBlock, 0, s>>>(M, j + 1, gd,
+                                                                                                    G.partial, hh);
                 CU_LAUNCH(ctx);
                 if (pass == 0) {
                     k_update<T><<<nblk(N), kBlock, 0, s>>>(n, M, j + 1, G.V, vs, hh, w);
+                    CU_LAUNCH(ctx);
                 } else {
-                    k_update_norm<T><<<dim3(g1, mp.mchunks), kBlock, kBlock * sizeof(double), s>>>(
-                        n, M, mp.MB, mp.RB, j + 1, G.V, vs, hh, w, G.partial);
+                    int g1 = grid_rows(n, mp, 1);
+                    k_update_norm<T><<<dim3(g1, mp.mchunks), kBlock, 0, s>>>(n, M, mp.MB, mp.RB, j + 1, G.V, vs, hh,
+                                                                             w, G.partial);
+                    CU_LAUNCH(ctx);
+                    k_reduce<<<wblk, kBlock, 0, s>>>(M, 1, g1, G.partial, G.nrm2);
+                    CU_LAUNCH(ctx);
                 }
-                CU_LAUNCH(ctx);
             }
             CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
-            k_givens<<<(M + 127) / 128, 128, 0, s>>>(M, g1, R, j, G.h, G.h2, G.partial, G.H, G.cs, G.sn, G.g,
-                                                     G.beta, G.active, G.kcol, G.its, G.resid, G.bnorm, tol,
+            k_givens<<<(M + 127) / 128, 128, 0, s>>>(M, R, j, G.h, G.h2, G.nrm2, G.H, G.cs, G.sn, G.g, G.beta,
+                                                     G.active, G.kcol, G.its, G.resid, G.bnorm, tol,
                                                      G.d_active_count);
             CU_LAUNCH(ctx);
-            k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, w, G.beta, dinv, G.Z);
-            CU_LAUNCH(ctx);
             jlast = j;
-            if ((j + 1) % check_every == 0 || j + 1 == R) {
+            bool check = (j + 1) % check_every == 0 || j + 1 == R;
+            if (check) {
                 CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
                 CU(ctx, cudaStreamSynchronize(s));
                 if (*G.h_active == 0) break;
             }
+            k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, w, G.beta);
+            CU_LAUNCH(ctx);
+            z = precond(w, G.Z);
+            if (!z) return MLPG_ERR_CUDA;
         }
         k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y);
         CU_LAUNCH(ctx);
-        k_xupdate<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, G.y, G.kcol, dinv, x);
+        k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, G.y, G.kcol, G.W);
         CU_LAUNCH(ctx);
-        // iterations of this cycle
+        const T *u = precond(G.W, G.Z);
+        if (!u) return MLPG_ERR_CUDA;
+        k_axpy1<T><<<nblk(N), kBlock, 0, s>>>(N, u, x);
+        CU_LAUNCH(ctx);
         std::vector<int> its(M);
         CU(ctx, cudaMemcpyAsync(its.data(), G.its, sizeof(int) * M, cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
@@ -421,8 +471,9 @@ mlpg_status inner_solve<double>(mlpg_ctx *ctx, const double *b, double *x, doubl
     MLPG_TRY(gmres_alloc(ctx, ctx->g64, ctx->n, ctx->m, ctx->opt.inner_restart));
     CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * ctx->n * ctx->m, ctx->stream));
     ApplyFn<double> A = [ctx](const double *X, const double *B, double *Y) { return apply_L64_res(ctx, X, B, Y); };
+    PrecFn<double> P = [ctx](const double *v, double *z) { return apply_prec<double>(ctx, v, z); };
     int64_t its = 0;
-    mlpg_status st = gmres_solve<double>(ctx, ctx->g64, A, ctx->dinv64, b, x, tol, ctx->opt.max_inner,
+    mlpg_status st = gmres_solve<double>(ctx, ctx->g64, A, P, b, x, tol, ctx->opt.max_inner,
                                          ctx->opt.check_every, &its);
     ctx->st.last_inner_iters += its;
     ctx->st.last_inner_solves += 1;
@@ -434,8 +485,9 @@ mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double t
     MLPG_TRY(gmres_alloc(ctx, ctx->g32, ctx->n, ctx->m, ctx->opt.inner_restart));
     CU(ctx, cudaMemsetAsync(x, 0, sizeof(float) * ctx->n * ctx->m, ctx->stream));
     ApplyFn<float> A = [ctx](const float *X, const float *B, float *Y) { return apply_L32_res(ctx, X, B, Y); };
+    PrecFn<float> P = [ctx](const float *v, float *z) { return apply_prec<float>(ctx, v, z); };
     int64_t its = 0;
-    mlpg_status st = gmres_solve<float>(ctx, ctx->g32, A, ctx->dinv32, b, x, tol, ctx->opt.max_inner,
+    mlpg_status st = gmres_solve<float>(ctx, ctx->g32, A, P, b, x, tol, ctx->opt.max_inner,
                                         ctx->opt.check_every, &its);
     ctx->st.last_inner_iters += its;
     ctx->st.last_inner_solves += 1;
@@ -504,7 +556,8 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     };
     ctx->cur_inner_tol = inner_tol;
     int64_t oits = 0;
-    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, nullptr, bphi, phi, outer_tol, ctx->opt.max_outer, 1, &oits));
+    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol, ctx->opt.max_outer, 1,
+                                 &oits));
     ctx->st.last_outer_iters += (int32_t)oits;
     // recovery Psi = L^{-1} MS Phi + b_psi
     MLPG_TRY(apply_MS<T>(ctx, phi, rhs));
@@ -519,7 +572,7 @@ static mlpg_status global_norm(mlpg_ctx *ctx, const double *a, int64_t N, double
     int64_t G = std::min<int64_t>(1024, nblk(N));
     k_sumsq<<<G, kBlock, 0, ctx->stream>>>(N, a, ctx->red);
     CU_LAUNCH(ctx);
-    k_reduce<<<1, 128, 0, ctx->stream>>>(1, 1, (int)G, ctx->red, ctx->red + 2048);
+    k_reduce<<<1, 32, 0, ctx->stream>>>(1, 1, (int)G, ctx->red, ctx->red + 2048);
     CU_LAUNCH(ctx);
     CU(ctx, cudaMemcpyAsync(out_host_slot, ctx->red + 2048, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     return MLPG_OK;

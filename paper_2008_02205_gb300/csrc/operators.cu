@@ -17,6 +17,7 @@
 // FP32 path: the six arrays are streamed once per apply and combined per
 // direction in registers; the face terms live in a separate short segment
 // per boundary row.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -366,6 +367,122 @@ __global__ void k_interp_apply(int64_t n, const int32_t *__restrict__ rowptr, co
     out[i] = s;
 }
 
+
+// ---------------------------------------------------------------------------
+// Block-Jacobi preconditioner.  Points are grouped into Morton-ordered blocks
+// of B = MLPG_BLOCK_PTS; for every (block, direction) the dense B x B diagonal
+// block of L_m is inverted (Gauss-Jordan with partial pivoting, FP32, one warp;
+// lane l owns column l of the augmented [A | I]).  The inverse is stored
+// [block][row][col][m] so that the apply reads it coalesced across directions.
+// ---------------------------------------------------------------------------
+constexpr int kB = MLPG_BLOCK_PTS;
+
+__global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const int32_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ col, int64_t nnz,
+                                                   const double *__restrict__ A64, const double *__restrict__ Sf,
+                                                   const double *__restrict__ coef, const double *__restrict__ fcoef,
+                                                   const int32_t *__restrict__ bmember,
+                                                   const int32_t *__restrict__ bof, float *__restrict__ Pinv,
+                                                   int *__restrict__ flag) {
+    __shared__ float sA[8][kB][2 * kB + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t k = blockIdx.x;
+    const int dir = blockIdx.y * 8 + warp;
+    if (dir >= m) return;
+    float(*A)[2 * kB + 1] = sA[warp];
+    const double *c = coef + 8 * dir, *fc = fcoef + 4 * dir;
+    if (lane < kB) {
+        const int a = lane;
+        for (int b = 0; b < 2 * kB; ++b) A[a][b] = (b == kB + a) ? 1.0f : 0.0f;
+        const int32_t i = bmember[k * kB + a];
+        if (i < 0) {
+            A[a][a] = 1.0f;
+        } else {
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                int32_t sl = bof[col[p]];
+                if (sl / kB != k) continue;
+                double v = A64[p];
+                for (int q = 1; q < 6; ++q) v += c[q] * A64[q * nnz + p];
+                for (int f = 0; f < 4; ++f) v += fc[f] * Sf[f * nnz + p];
+                A[a][sl - k * kB] = (float)v;
+            }
+        }
+    }
+    __syncwarp();
+    bool singular = false;
+    for (int cc = 0; cc < kB; ++cc) {
+        int piv = cc;
+        float best = fabsf(A[cc][cc]);
+        for (int r = cc + 1; r < kB; ++r) {
+            float v = fabsf(A[r][cc]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (!(best > 0.0f)) { singular = true; break; }
+        __syncwarp();
+        if (piv != cc) {
+            float t = A[cc][lane];
+            A[cc][lane] = A[piv][lane];
+            A[piv][lane] = t;
+        }
+        __syncwarp();
+        const float inv = 1.0f / A[cc][cc];
+        __syncwarp();
+        A[cc][lane] *= inv;
+        __syncwarp();
+        float fr[kB];
+#pragma unroll
+        for (int r = 0; r < kB; ++r) fr[r] = A[r][cc];
+        __syncwarp();
+        const float pc = A[cc][lane];
+#pragma unroll
+        for (int r = 0; r < kB; ++r)
+            if (r != cc) A[r][lane] -= fr[r] * pc;
+        __syncwarp();
+    }
+    if (singular) {
+        if (lane == 0) atomicOr(flag, 32);
+        return;
+    }
+    for (int e = lane; e < kB * kB; e += 32) {
+        int a = e / kB, b = e - a * kB;
+        Pinv[((k * kB + a) * kB + b) * (int64_t)m + dir] = A[a][kB + b];
+    }
+}
+
+template <int DPL, typename T>
+__global__ void __launch_bounds__(256) k_bjacobi(int64_t n, int m, int tm_log2, const int32_t *__restrict__ bof,
+                                                 const int32_t *__restrict__ bmember,
+                                                 const float *__restrict__ Pinv, const T *__restrict__ v,
+                                                 T *__restrict__ z) {
+    const int TM = 1 << tm_log2;
+    const int lane = threadIdx.x & (TM - 1);
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
+    if (i >= n) return;
+    const int32_t slot = bof[i];
+    const int64_t blk = slot / kB;
+    T acc[DPL];
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) acc[t] = (T)0;
+    const float *prow = Pinv + (int64_t)slot * kB * m;
+#pragma unroll 4
+    for (int b = 0; b < kB; ++b) {
+        const int32_t j = bmember[blk * kB + b];
+        if (j < 0) continue;
+        const float *pv = prow + (int64_t)b * m;
+        const T *vv = v + (int64_t)j * m;
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int kk = lane + t * TM;
+            if (kk < m) acc[t] += (T)pv[kk] * vv[kk];
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) {
+        int kk = lane + t * TM;
+        if (kk < m) z[i * m + kk] = acc[t];
+    }
+}
+
 struct Team {
     int tm_log2, dpl;
 };
@@ -418,6 +535,7 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     MLPG_TRY(dalloc(ctx, &ctx->dinv32, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->r64, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->abc, 3 * n));
+    MLPG_TRY(dalloc(ctx, &ctx->Pinv, (size_t)ctx->nblk * kB * kB * m));
     // boundary segment (the face arrays do not depend on dt)
     int *cnt;
     MLPG_TRY(dalloc(ctx, &cnt, n));
@@ -465,6 +583,16 @@ mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
     CU(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(ctx, cudaStreamSynchronize(s));
     if (flag & 16) return set_err(ctx, MLPG_ERR_ARG, "transport operator has a zero diagonal entry");
+    // block-Jacobi inverses of every direction
+    {
+        dim3 grid((unsigned)ctx->nblk, (unsigned)((m + 7) / 8));
+        k_block_inv<<<grid, 256, 0, s>>>(ctx->nblk, m, ctx->rowptr, ctx->col, nnz, ctx->A64, Sf, ctx->coef,
+                                         ctx->fcoef, ctx->bmember, ctx->bof, ctx->Pinv, ctx->d_flag);
+        CU_LAUNCH(ctx);
+        CU(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+        if (flag & 32) return set_err(ctx, MLPG_ERR_ARG, "singular diagonal block in the transport operator");
+    }
     ctx->kappa = kappa;
     for (int f = 0; f < 6; ++f) ctx->ops_psib[f] = ctx->psi_b[f];
     ctx->st.spmm_bytes = 0;
@@ -534,6 +662,60 @@ mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out) {
 }
 template mlpg_status apply_MS<double>(mlpg_ctx *, const double *, double *);
 template mlpg_status apply_MS<float>(mlpg_ctx *, const double *, float *);
+
+template <typename T>
+mlpg_status apply_prec(mlpg_ctx *ctx, const T *v, T *z) {
+    Team tm = pick_team(ctx->m);
+    int64_t grid = team_grid(ctx->n, tm);
+    cudaStream_t s = ctx->stream;
+    switch (tm.dpl) {
+        case 1: k_bjacobi<1, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+        case 2: k_bjacobi<2, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+        case 3: k_bjacobi<3, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+        case 4: k_bjacobi<4, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+        case 5: case 6: k_bjacobi<6, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+        case 7: case 8: k_bjacobi<8, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+        default: k_bjacobi<16, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+    }
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+template mlpg_status apply_prec<double>(mlpg_ctx *, const double *, double *);
+template mlpg_status apply_prec<float>(mlpg_ctx *, const float *, float *);
+
+// Morton order of the points (host, once per point set) cut into blocks of
+// MLPG_BLOCK_PTS consecutive points.
+mlpg_status build_blocks(mlpg_ctx *ctx) {
+    const int64_t n = ctx->n;
+    const int d = ctx->dim;
+    std::vector<std::pair<uint64_t, int32_t>> key(n);
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t code = 0;
+        uint32_t qv[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+            double t = (ctx->h_x[i * d + a] - ctx->opt.lo[a]) / (ctx->opt.hi[a] - ctx->opt.lo[a]);
+            t = t < 0 ? 0 : (t > 1 ? 1 : t);
+            qv[a] = (uint32_t)(t * 1048575.0);
+        }
+        for (int b = 19; b >= 0; --b)
+            for (int a = d - 1; a >= 0; --a) code = (code << 1) | ((qv[a] >> b) & 1u);
+        key[i] = {code, (int32_t)i};
+    }
+    std::sort(key.begin(), key.end());
+    ctx->nblk = (n + kB - 1) / kB;
+    std::vector<int32_t> member(ctx->nblk * kB, -1), bof(n);
+    for (int64_t r = 0; r < n; ++r) {
+        member[r] = key[r].second;
+        bof[key[r].second] = (int32_t)r;
+    }
+    MLPG_TRY(dalloc(ctx, &ctx->bmember, ctx->nblk * kB));
+    MLPG_TRY(dalloc(ctx, &ctx->bof, n));
+    CU(ctx, cudaMemcpyAsync(ctx->bmember, member.data(), member.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            ctx->stream));
+    CU(ctx, cudaMemcpyAsync(ctx->bof, bof.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return MLPG_OK;
+}
 
 mlpg_status interp_flux(mlpg_ctx *ctx, double *out_dev, int kind) {
     const int64_t n = ctx->n;
