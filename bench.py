@@ -184,7 +184,9 @@ def main():
     if args.be_steps is not None:
         prob.steps = args.be_steps
     prec = pkg.MLPG_MIXED if args.precision == "mixed" else pkg.MLPG_FP64
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream: the library runs on it and the CUDA events below are recorded on it
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     opts = dict(precision=prec, stream=stream.cuda_stream)
     host = dict(x=prob.x, R=prob.R, om=prob.omega, w=prob.w, st=prob.sigma_t, ss=prob.sigma_s, q=prob.q)
     dv = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in host.items()}

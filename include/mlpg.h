@@ -52,14 +52,15 @@ typedef struct {
     int precision;         /* mlpg_precision; default MLPG_FP64 */
     double inner_tol;      /* per-direction transport GMRES: ||r|| <= tol ||b||; default 1e-12 */
     double outer_tol;      /* scattering GMRES on Phi (Eq. krylov-operator); default 1e-12 */
-    int inner_restart;     /* inner GMRES restart length (<= 64); default 30 */
-    int outer_restart;     /* outer GMRES restart length (<= 128); default 60 */
+    int inner_restart;     /* inner GMRES restart length (<= 32); default 20 (FP64), mixed_restart in MLPG_MIXED */
+    int outer_restart;     /* outer GMRES restart length (<= 32); default 30 */
     int max_inner;         /* inner iteration cap per solve; default 2000 */
     int max_outer;         /* outer iteration cap per solve; default 500 */
     double refine_tol;     /* MLPG_MIXED: FP64 step residual ||R|| <= tol ||f||; default 1e-11 */
     int max_refine;        /* MLPG_MIXED: refinement sweeps per step; default 12 */
     double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-5 */
     int check_every;       /* inner GMRES: host convergence check interval (steps); default 4 */
+    int mixed_restart;     /* MLPG_MIXED: restart length of the FP32 inner GMRES (<= 32); default 10 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
 } mlpg_options;
 

@@ -65,7 +65,7 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
     if (opt->dim != 2 || n < 4 || m < 1 || m > MLPG_MAX_DIR) return MLPG_ERR_ARG;
     if (n >= (int64_t(1) << 31)) return MLPG_ERR_ARG;
     if (opt->inner_restart < 1 || opt->inner_restart > MLPG_MAX_RESTART || opt->outer_restart < 1 ||
-        opt->outer_restart > MLPG_MAX_RESTART || opt->check_every < 1 || !(opt->c > 0) ||
+        opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
     for (int a = 0; a < opt->dim; ++a)
@@ -198,14 +198,15 @@ void mlpg_default_options(mlpg_options *o) {
     o->precision = MLPG_FP64;
     o->inner_tol = 1e-12;
     o->outer_tol = 1e-12;
-    o->inner_restart = 30;
-    o->outer_restart = 60;
+    o->inner_restart = 20;
+    o->outer_restart = 30;
     o->max_inner = 2000;
     o->max_outer = 500;
     o->refine_tol = 1e-11;
     o->max_refine = 12;
     o->mixed_inner_tol = 1e-5;
     o->check_every = 4;
+    o->mixed_restart = 10;
     o->stream = nullptr;
 }
 

@@ -11,7 +11,7 @@
 #include "mlpg.h"
 
 #define MLPG_MAX_DIR 1024   // directions per problem (one thread per direction in a block row)
-#define MLPG_MAX_RESTART 64 // inner / outer restart length cap for the device Hessenberg arrays
+#define MLPG_MAX_RESTART 32 // restart length cap (Gram-Schmidt keeps one accumulator per basis vector in registers)
 #define MLPG_MAX_CELL_FUNCS 40  // functions whose support can reach one 2D cell
 #define MLPG_BLOCK_PTS 16       // points per block of the block-Jacobi preconditioner
 
@@ -68,6 +68,7 @@ struct Gmres {
     double *h = nullptr;   // (R + 1) * M : dot results of the current step
     double *h2 = nullptr;  // (R + 1) * M
     double *y = nullptr;   // R * M
+    float *y32 = nullptr;  // R * M: float copy of y
     double *bnorm = nullptr, *beta = nullptr, *resid = nullptr;  // M
     double *nrm2 = nullptr;  // M: squared norms of the current vector
     int *active = nullptr; // M: 1 while iterating in this cycle
@@ -123,10 +124,13 @@ struct mlpg_ctx {
     float *A32 = nullptr;       // [6][nnz]
     int64_t nb = 0;             // boundary-segment entries
     int32_t *bptr = nullptr, *bcol = nullptr;
+    int32_t *brow = nullptr;    // rows with face terms (nbrow of them)
+    int64_t nbrow = 0;
     float *bval32 = nullptr;    // [2 dim][nb]
     double *bval64 = nullptr;   // [2 dim][nb]
     double *coef = nullptr;     // [m][8]: 1, Ox, Oy, Ox^2, Oy^2, OxOy, (unused x2)
     double *fcoef = nullptr;    // [m][2 dim]: max(Omega . n_f, 0)
+    float *coef32 = nullptr;    // [m][16]: float copy of coef (0..7) and fcoef (8..11)
     double *dinv64 = nullptr;   // [n][m]
     float *dinv32 = nullptr;
     double *r64 = nullptr;      // [n][m] boundary + volume source

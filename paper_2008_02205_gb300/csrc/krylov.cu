@@ -41,9 +41,10 @@ Map2 map2(int M) {
     r.mchunks = (M + r.MB - 1) / r.MB;
     return r;
 }
+constexpr int kRowBlocks = 8 * 152;   // row blocks of the streaming passes (about 8 per SM)
 int grid_rows(int64_t n, const Map2 &mp, int nl) {
     int64_t maxg = (n + mp.RB - 1) / mp.RB;
-    int64_t g = (2 * 152 + mp.mchunks * nl - 1) / (mp.mchunks * nl);
+    int64_t g = (kRowBlocks + mp.mchunks * nl - 1) / (mp.mchunks * nl);
     if (g > maxg) g = maxg;
     if (g < 1) g = 1;
     return (int)g;
@@ -144,6 +145,75 @@ __global__ void __launch_bounds__(kBlock) k_update_norm(int64_t n, int M, int MB
     }
 }
 
+// One fused pass of classical Gram-Schmidt over the basis V_0..V_{nl-1}
+// (all in registers for nl <= MAXL; each thread owns one system m and a
+// strided set of rows):
+//   MODE 0:  h_l = V_l . w
+//   MODE 1:  w <- w - sum_l hin_l V_l, then h_l = V_l . w
+//   MODE 2:  w <- w - sum_l hin_l V_l, then ||w||^2
+// Block sums go to partial[(l * G + block) * M + m].
+template <typename T, int MAXL, int MODE>
+__global__ void __launch_bounds__(kBlock) k_cgs(int64_t n, int M, int MB, int RB, int nl,
+                                                const T *__restrict__ V, int64_t vs,
+                                                const double *__restrict__ hin, T *__restrict__ w,
+                                                double *__restrict__ partial) {
+    using A = typename Arith<T>::type;
+    constexpr int NACC = MODE == 2 ? 1 : MAXL;
+    __shared__ double sh[kBlock];
+    const int t = threadIdx.x, ml = t % MB, r = t / MB;
+    const int m = blockIdx.y * MB + ml, G = gridDim.x;
+    const bool act = r < RB && m < M;
+    A acc[NACC], hl[MAXL];
+#pragma unroll
+    for (int l = 0; l < NACC; ++l) acc[l] = 0;
+#pragma unroll
+    for (int l = 0; l < MAXL; ++l) hl[l] = (MODE >= 1 && act && l < nl) ? (A)hin[l * M + m] : (A)0;
+    if (act) {
+        const int64_t stride = (int64_t)G * RB;
+        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += stride) {
+            const int64_t e = i * M + m;
+            A wv = (A)w[e];
+            if (MODE >= 1) {
+#pragma unroll
+                for (int l = 0; l < MAXL; ++l)
+                    if (l < nl) wv -= hl[l] * (A)V[l * vs + e];
+                w[e] = (T)wv;
+                wv = (A)(T)wv;
+            }
+            if (MODE <= 1) {
+#pragma unroll
+                for (int l = 0; l < MAXL; ++l)
+                    if (l < nl) acc[l] += (A)V[l * vs + e] * wv;
+            } else {
+                acc[0] += wv * wv;
+            }
+        }
+    }
+    const int nout = MODE == 2 ? 1 : nl;
+#pragma unroll
+    for (int l = 0; l < NACC; ++l) {
+        if (l < nout) {
+            sh[t] = act ? (double)acc[l] : 0.0;
+            __syncthreads();
+            if (r == 0 && m < M) {
+                double s = 0.0;
+                for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
+                partial[((int64_t)l * G + blockIdx.x) * M + m] = s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T, int MODE>
+static void launch_cgs(dim3 grid, cudaStream_t s, int64_t n, int M, int MB, int RB, int nl, const T *V,
+                       int64_t vs, const double *hin, T *w, double *partial) {
+    if (nl <= 4) k_cgs<T, 4, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
+    else if (nl <= 8) k_cgs<T, 8, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
+    else if (nl <= 16) k_cgs<T, 16, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
+    else k_cgs<T, 32, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
+}
+
 // Start of a cycle: beta = ||r|| (nrm2 = ||r||^2); decide which systems iterate.
 __global__ void k_start(int M, int R, const double *__restrict__ nrm2, double *__restrict__ bnorm,
                         double *__restrict__ g, double *__restrict__ sc, int *__restrict__ active,
@@ -210,18 +280,23 @@ __global__ void k_givens(int M, int R, int j, const double *__restrict__ h1, con
     }
 }
 
-// w = w * sc[m]
+// w = w * sc[m]  (in the vector's own precision)
 template <typename T>
 __global__ void k_scale(int64_t n, int M, T *__restrict__ w, const double *__restrict__ sc) {
+    using A = typename Arith<T>::type;
+    __shared__ A ssc[MLPG_MAX_DIR];
+    for (int k = threadIdx.x; k < M; k += blockDim.x) ssc[k] = (A)sc[k];
+    __syncthreads();
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * M) return;
     int m = (int)(e % M);
-    w[e] = (T)((double)w[e] * sc[m]);
+    w[e] = (T)((A)w[e] * ssc[m]);
 }
 
-// y = R^{-1} g per system (upper triangular part of the rotated Hessenberg)
+// y = R^{-1} g per system (upper triangular part of the rotated Hessenberg);
+// also a float copy for FP32 vectors
 __global__ void k_backsolve(int M, int R, const double *__restrict__ H, const double *__restrict__ g,
-                            const int *__restrict__ kcol, double *__restrict__ y) {
+                            const int *__restrict__ kcol, double *__restrict__ y, float *__restrict__ y32) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     int k = kcol[m];
@@ -230,20 +305,29 @@ __global__ void k_backsolve(int M, int R, const double *__restrict__ H, const do
         double s = g[m * (R + 1) + r];
         for (int c = r + 1; c < k; ++c) s -= Hm[r * R + c] * y[c * M + m];
         y[r * M + m] = Hm[r * R + r] != 0.0 ? s / Hm[r * R + r] : 0.0;
+        y32[r * M + m] = (float)y[r * M + m];
     }
 }
 
-// u = sum_{l < kcol[m]} y_l V_l
+template <typename T>
+static const typename Arith<T>::type *y_of(const Gmres<T> &G);
+template <>
+const double *y_of<double>(const Gmres<double> &G) { return G.y; }
+template <>
+const float *y_of<float>(const Gmres<float> &G) { return G.y32; }
+
+// u = sum_{l < kcol[m]} y_l V_l, with y already in the vector's arithmetic type
 template <typename T>
 __global__ void k_combine(int64_t n, int M, int kmax, const T *__restrict__ V, int64_t vstride,
-                          const double *__restrict__ y, const int *__restrict__ kcol, T *__restrict__ u) {
+                          const typename Arith<T>::type *__restrict__ y, const int *__restrict__ kcol,
+                          T *__restrict__ u) {
     using A = typename Arith<T>::type;
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * M) return;
     int m = (int)(e % M);
     int k = min(kcol[m], kmax);
     A s = 0;
-    for (int l = 0; l < k; ++l) s += (A)y[l * M + m] * (A)V[l * vstride + e];
+    for (int l = 0; l < k; ++l) s += y[l * M + m] * (A)V[l * vstride + e];
     u[e] = (T)s;
 }
 
@@ -257,11 +341,13 @@ __global__ void k_axpy1(int64_t N, const T *__restrict__ u, T *__restrict__ x) {
 template <typename T>
 __global__ void k_Dreduce(int64_t n, int M, const double *__restrict__ w, const T *__restrict__ x,
                           double *__restrict__ out) {
+    using A = typename Arith<T>::type;
     int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= n) return;
-    double s = 0.0;
-    for (int m = lane; m < M; m += 32) s += w[m] * (double)x[i * M + m];
+    A sl = 0;
+    for (int m = lane; m < M; m += 32) sl += (A)w[m] * (A)x[i * M + m];
+    double s = (double)sl;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) out[i] = s;
 }
@@ -325,6 +411,7 @@ static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int
     MLPG_TRY(dalloc(ctx, &G.h, (size_t)(R + 1) * M));
     MLPG_TRY(dalloc(ctx, &G.h2, (size_t)(R + 1) * M));
     MLPG_TRY(dalloc(ctx, &G.y, (size_t)R * M));
+    MLPG_TRY(dalloc(ctx, &G.y32, (size_t)R * M));
     MLPG_TRY(dalloc(ctx, &G.bnorm, M));
     MLPG_TRY(dalloc(ctx, &G.nrm2, M));
     MLPG_TRY(dalloc(ctx, &G.beta, M));   // scale factors 1/||w||
@@ -332,8 +419,8 @@ static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int
     MLPG_TRY(dalloc(ctx, &G.active, M));
     MLPG_TRY(dalloc(ctx, &G.kcol, M));
     MLPG_TRY(dalloc(ctx, &G.its, M));
-    // k_dots writes G * nl * M partials with G = ceil(304 / (mchunks nl)) <= 304 / mchunks + 1
-    G.partial_cap = (int64_t)(2 * 152 + MLPG_MAX_RESTART + 8) * M;
+    // the fused Gram-Schmidt passes write G * nl * M partials with G <= kRowBlocks, nl <= R + 1
+    G.partial_cap = (int64_t)kRowBlocks * (R + 1) * M;
     MLPG_TRY(dalloc(ctx, &G.partial, G.partial_cap));
     MLPG_TRY(dalloc(ctx, &G.d_active_count, 1));
     void *hp = nullptr;
@@ -403,27 +490,26 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         for (int j = 0; j < R; ++j) {
             T *w = G.V + (j + 1) * vs;
             MLPG_TRY(A(z, nullptr, w));
-            for (int pass = 0; pass < 2; ++pass) {
-                double *hh = pass == 0 ? G.h : G.h2;
-                int gd = grid_rows(n, mp, j + 1);
-                if ((int64_t)gd * (j + 1) * mp.mchunks * mp.MB > G.partial_cap)
+            {
+                // CGS2 in three fused passes over V_0..V_j
+                // fewer, longer-running blocks as the basis grows (bounded partial sums)
+                const int nl = j + 1, g1 = grid_rows(n, mp, (nl + 3) / 4);
+                const dim3 grid(g1, mp.mchunks);
+                if ((int64_t)g1 * nl * mp.mchunks * mp.MB > G.partial_cap)
                     return set_err(ctx, MLPG_ERR_ARG, "reduction buffer too small");
-                k_dots<T><<<dim3(gd, mp.mchunks, j + 1), kBlock, 0, s>>>(n, M, mp.MB, mp.RB, G.V, vs, w, G.partial);
+                const int rblk = (int)(((int64_t)nl * M * 32 + kBlock - 1) / kBlock);
+                launch_cgs<T, 0>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, nullptr, w, G.partial);
                 CU_LAUNCH(ctx);
-                k_reduce<<<(int)(((int64_t)(j + 1) * M * 32 + kBlock - 1) / kBlock), kBlock, 0, s>>>(M, j + 1, gd,
-                                                                                                    G.partial, hh);
+                k_reduce<<<rblk, kBlock, 0, s>>>(M, nl, g1, G.partial, G.h);
                 CU_LAUNCH(ctx);
-                if (pass == 0) {
-                    k_update<T><<<nblk(N), kBlock, 0, s>>>(n, M, j + 1, G.V, vs, hh, w);
-                    CU_LAUNCH(ctx);
-                } else {
-                    int g1 = grid_rows(n, mp, 1);
-                    k_update_norm<T><<<dim3(g1, mp.mchunks), kBlock, 0, s>>>(n, M, mp.MB, mp.RB, j + 1, G.V, vs, hh,
-                                                                             w, G.partial);
-                    CU_LAUNCH(ctx);
-                    k_reduce<<<wblk, kBlock, 0, s>>>(M, 1, g1, G.partial, G.nrm2);
-                    CU_LAUNCH(ctx);
-                }
+                launch_cgs<T, 1>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.h, w, G.partial);
+                CU_LAUNCH(ctx);
+                k_reduce<<<rblk, kBlock, 0, s>>>(M, nl, g1, G.partial, G.h2);
+                CU_LAUNCH(ctx);
+                launch_cgs<T, 2>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.h2, w, G.partial);
+                CU_LAUNCH(ctx);
+                k_reduce<<<wblk, kBlock, 0, s>>>(M, 1, g1, G.partial, G.nrm2);
+                CU_LAUNCH(ctx);
             }
             CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
             k_givens<<<(M + 127) / 128, 128, 0, s>>>(M, R, j, G.h, G.h2, G.nrm2, G.H, G.cs, G.sn, G.g, G.beta,
@@ -442,9 +528,9 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
             z = precond(w, G.Z);
             if (!z) return MLPG_ERR_CUDA;
         }
-        k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y);
+        k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y, G.y32);
         CU_LAUNCH(ctx);
-        k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, G.y, G.kcol, G.W);
+        k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, y_of<T>(G), G.kcol, G.W);
         CU_LAUNCH(ctx);
         const T *u = precond(G.W, G.Z);
         if (!u) return MLPG_ERR_CUDA;
@@ -482,7 +568,7 @@ mlpg_status inner_solve<double>(mlpg_ctx *ctx, const double *b, double *x, doubl
 
 template <>
 mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double tol) {
-    MLPG_TRY(gmres_alloc(ctx, ctx->g32, ctx->n, ctx->m, ctx->opt.inner_restart));
+    MLPG_TRY(gmres_alloc(ctx, ctx->g32, ctx->n, ctx->m, ctx->opt.mixed_restart));
     CU(ctx, cudaMemsetAsync(x, 0, sizeof(float) * ctx->n * ctx->m, ctx->stream));
     ApplyFn<float> A = [ctx](const float *X, const float *B, float *Y) { return apply_L32_res(ctx, X, B, Y); };
     PrecFn<float> P = [ctx](const float *v, float *z) { return apply_prec<float>(ctx, v, z); };

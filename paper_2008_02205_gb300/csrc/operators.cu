@@ -66,7 +66,7 @@ __global__ void k_form_arrays(int64_t nnz, double kappa, const int32_t *__restri
 }
 
 __global__ void k_coef(int m, const double *__restrict__ omega, double *__restrict__ coef,
-                       double *__restrict__ fcoef) {
+                       double *__restrict__ fcoef, float *__restrict__ coef32) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
     double ox = omega[3 * k], oy = omega[3 * k + 1];
@@ -77,6 +77,11 @@ __global__ void k_coef(int m, const double *__restrict__ omega, double *__restri
     fcoef[4 * k + 1] = fmax(ox, 0.0);
     fcoef[4 * k + 2] = fmax(-oy, 0.0);
     fcoef[4 * k + 3] = fmax(oy, 0.0);
+    // float copy for the FP32 kernels: [k][0..7] = 1, c1..c5, 0, 0 and the faces at [k][8..11]
+    float *c32 = coef32 + 16 * k;
+    for (int q = 0; q < 8; ++q) c32[q] = (float)c[q];
+    for (int f = 0; f < 4; ++f) c32[8 + f] = (float)fcoef[4 * k + f];
+    for (int q = 12; q < 16; ++q) c32[q] = 0.0f;
 }
 
 __global__ void k_materialize(int64_t nnz, int m, const double *__restrict__ A64,
@@ -187,6 +192,17 @@ __global__ void k_scan1(int64_t n, const int *__restrict__ in, int32_t *__restri
 // batched L-apply.  A team of TM lanes (power of two) works on one row; lane l
 // owns directions m = l + TM t, t < DPL.  Y = L X, or Y = B - L X when B != 0.
 // ---------------------------------------------------------------------------
+// Warp-per-row layout of the FP64 apply: the 32 lanes of a warp are S
+// entry slots x TM direction lanes (S * TM = 32); lane (s, l) takes the row
+// entries p0 + s, p0 + s + S, ... and the directions l, l + TM, ... (DPL of
+// them).  The S partial sums of each direction are combined with shuffles.
+template <typename T, int DPL>
+__device__ __forceinline__ void slot_reduce(T (&acc)[DPL], int TM) {
+#pragma unroll
+    for (int t = 0; t < DPL; ++t)
+        for (int o = TM; o < 32; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+}
+
 template <int DPL>
 __global__ void __launch_bounds__(256) k_spmm64(int64_t n, int m, int tm_log2,
                                                 const int32_t *__restrict__ rowptr,
@@ -194,44 +210,62 @@ __global__ void __launch_bounds__(256) k_spmm64(int64_t n, int m, int tm_log2,
                                                 const double *__restrict__ L64,
                                                 const double *__restrict__ X, const double *__restrict__ B,
                                                 double *__restrict__ Y) {
-    const int TM = 1 << tm_log2;
-    const int lane = threadIdx.x & (TM - 1);
-    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
+    const int TM = 1 << tm_log2, S = 32 >> tm_log2;
+    const int lane = threadIdx.x & (TM - 1), slot = (threadIdx.x & 31) >> tm_log2;
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (row >= n) return;
     double acc[DPL];
 #pragma unroll
     for (int t = 0; t < DPL; ++t) acc[t] = 0.0;
-    const int32_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    for (int32_t p = p0; p < p1; ++p) {
-        const int64_t j = col[p];
-        const double *lv = L64 + (int64_t)p * m;
-        const double *xv = X + j * m;
+    const int32_t p1 = rowptr[row + 1];
+    int32_t p = rowptr[row] + slot;
+    for (; p + S < p1; p += 2 * S) {  // two entries per lane in flight
+        const int64_t j0 = col[p], j1 = col[p + S];
 #pragma unroll
         for (int t = 0; t < DPL; ++t) {
             int k = lane + t * TM;
-            if (k < m) acc[t] = fma(lv[k], xv[k], acc[t]);
+            if (k < m) {
+                double l0 = L64[(int64_t)p * m + k], l1 = L64[(int64_t)(p + S) * m + k];
+                double x0 = X[j0 * m + k], x1 = X[j1 * m + k];
+                acc[t] = fma(l0, x0, acc[t]);
+                acc[t] = fma(l1, x1, acc[t]);
+            }
         }
     }
+    if (p < p1) {
+        const int64_t j = col[p];
 #pragma unroll
-    for (int t = 0; t < DPL; ++t) {
-        int k = lane + t * TM;
-        if (k < m) {
-            int64_t e = row * m + k;
-            Y[e] = B ? B[e] - acc[t] : acc[t];
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) acc[t] = fma(L64[(int64_t)p * m + k], X[j * m + k], acc[t]);
+        }
+    }
+    slot_reduce<double, DPL>(acc, TM);
+    if (slot == 0) {
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) {
+                int64_t e = row * m + k;
+                Y[e] = B ? B[e] - acc[t] : acc[t];
+            }
         }
     }
 }
 
-template <int DPL>
-__global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, int64_t nnz, int64_t nb,
+// FP32 batched L-apply: a team of TM lanes per row (4 rows per warp for
+// TM = 8), lane l owns directions l, l + TM, ... (DPL of them; EXACT when
+// TM * DPL = m so no lane needs a guard).  The six operator values of an
+// entry are combined with the direction coefficients in registers.  The
+// outflow-face terms of the few boundary rows are added by k_faces32 (kept
+// out of this loop: a second loop here slows the main one down by half).
+// IDX is the index type of the [n][m] vectors (int when n * m < 2^31).
+template <int DPL, bool EXACT, typename IDX>
+__global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, int64_t nnz,
                                                 const int32_t *__restrict__ rowptr,
                                                 const int32_t *__restrict__ col,
                                                 const float *__restrict__ A32,
-                                                const int32_t *__restrict__ bptr,
-                                                const int32_t *__restrict__ bcol,
-                                                const float *__restrict__ bval,
-                                                const double *__restrict__ coef,
-                                                const double *__restrict__ fcoef,
+                                                const float *__restrict__ coef32,
                                                 const float *__restrict__ X, const float *__restrict__ B,
                                                 float *__restrict__ Y) {
     const int TM = 1 << tm_log2;
@@ -239,55 +273,93 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
     if (row >= n) return;
     float c1[DPL], c2[DPL], c3[DPL], c4[DPL], c5[DPL], acc[DPL];
+    bool on[DPL];
 #pragma unroll
     for (int t = 0; t < DPL; ++t) {
         int k = lane + t * TM;
-        k = k < m ? k : m - 1;
-        c1[t] = (float)coef[8 * k + 1];
-        c2[t] = (float)coef[8 * k + 2];
-        c3[t] = (float)coef[8 * k + 3];
-        c4[t] = (float)coef[8 * k + 4];
-        c5[t] = (float)coef[8 * k + 5];
+        on[t] = EXACT || k < m;
+        k = on[t] ? k : m - 1;
+        c1[t] = coef32[16 * k + 1];
+        c2[t] = coef32[16 * k + 2];
+        c3[t] = coef32[16 * k + 3];
+        c4[t] = coef32[16 * k + 4];
+        c5[t] = coef32[16 * k + 5];
         acc[t] = 0.0f;
     }
-    const int32_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    for (int32_t p = p0; p < p1; ++p) {
-        const int64_t j = col[p];
+    const int32_t p1 = rowptr[row + 1];
+    for (int32_t p = rowptr[row]; p < p1; ++p) {
+        const IDX jb = (IDX)col[p] * (IDX)m + (IDX)lane;
         const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
                     a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
-        const float *xv = X + j * m;
 #pragma unroll
         for (int t = 0; t < DPL; ++t) {
-            int k = lane + t * TM;
-            if (k < m) {
+            if (on[t]) {
                 float v = fmaf(c5[t], a5, fmaf(c4[t], a4, fmaf(c3[t], a3, fmaf(c2[t], a2, fmaf(c1[t], a1, a0)))));
-                acc[t] = fmaf(v, xv[k], acc[t]);
+                acc[t] = fmaf(v, X[jb + t * TM], acc[t]);
             }
         }
     }
-    const int32_t b0 = bptr[row], b1 = bptr[row + 1];
-    for (int32_t p = b0; p < b1; ++p) {
-        const int64_t j = bcol[p];
-        const float s0 = bval[p], s1 = bval[nb + p], s2 = bval[2 * nb + p], s3 = bval[3 * nb + p];
-        const float *xv = X + j * m;
-#pragma unroll
-        for (int t = 0; t < DPL; ++t) {
-            int k = lane + t * TM;
-            if (k < m) {
-                const double *fc = fcoef + 4 * k;
-                float v = (float)fc[0] * s0 + (float)fc[1] * s1 + (float)fc[2] * s2 + (float)fc[3] * s3;
-                acc[t] = fmaf(v, xv[k], acc[t]);
-            }
-        }
-    }
+    const IDX rb = (IDX)row * (IDX)m + (IDX)lane;
 #pragma unroll
     for (int t = 0; t < DPL; ++t) {
-        int k = lane + t * TM;
-        if (k < m) {
-            int64_t e = row * m + k;
+        if (on[t]) {
+            const IDX e = rb + t * TM;
             Y[e] = B ? B[e] - acc[t] : acc[t];
         }
     }
+}
+
+// Outflow-face terms sum_f max(Omega . n_f, 0) (S_f X)_i of the boundary
+// rows, subtracted from (residual form) or added to Y.  One warp per row of
+// the boundary-row list: 32 / TM entry slots x TM direction lanes, slot sums
+// combined with shuffles.
+template <int DPL>
+__global__ void __launch_bounds__(256) k_faces32(int64_t nbr, int m, int tm_log2, int64_t nb,
+                                                 const int32_t *__restrict__ brow,
+                                                 const int32_t *__restrict__ bptr,
+                                                 const int32_t *__restrict__ bcol,
+                                                 const float *__restrict__ bval,
+                                                 const float *__restrict__ coef32,
+                                                 const float *__restrict__ X, float sign,
+                                                 float *__restrict__ Y) {
+    const int TM = 1 << tm_log2, S = 32 >> tm_log2;
+    const int lane = threadIdx.x & (TM - 1), slot = (threadIdx.x & 31) >> tm_log2;
+    const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r >= nbr) return;
+    const int64_t row = brow[r];
+    float acc[DPL];
+#pragma unroll
+    for (int t = 0; t < DPL; ++t) acc[t] = 0.0f;
+    for (int32_t q = bptr[row] + slot; q < bptr[row + 1]; q += S) {
+        const int64_t jb = (int64_t)bcol[q] * m + lane;
+        const float s0 = bval[q], s1 = bval[nb + q], s2 = bval[2 * nb + q], s3 = bval[3 * nb + q];
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) {
+                const float *fc = coef32 + 16 * k + 8;
+                float v = fmaf(fc[0], s0, fmaf(fc[1], s1, fmaf(fc[2], s2, fc[3] * s3)));
+                acc[t] = fmaf(v, X[jb + t * TM], acc[t]);
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < DPL; ++t)
+        for (int o = TM; o < 32; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    if (slot == 0) {
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            int k = lane + t * TM;
+            if (k < m) Y[row * m + k] += sign * acc[t];
+        }
+    }
+}
+
+__global__ void k_brows(int64_t n, const int32_t *__restrict__ bptr, int32_t *__restrict__ brow,
+                        int *__restrict__ count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (bptr[i + 1] > bptr[i]) brow[atomicAdd(count, 1)] = (int32_t)i;
 }
 
 // RHS f[i][m] = (T_m X)_i + r[i][m] with T_m = T0 + Omega^x Tx + Omega^y Ty (FP64).
@@ -355,6 +427,22 @@ __global__ void k_ms_expand(int64_t n, int m, const double *__restrict__ abc,
     int k = (int)(e - i * m);
     double v = (abc[i] + coef[8 * k + 1] * abc[n + i] + coef[8 * k + 2] * abc[2 * n + i]) / kFourPi;
     out[e] = (T)v;
+}
+
+// FP32 variant: the three per-point products arrive pre-scaled by 1/(4 pi) in float
+__global__ void k_ms_expand32(int64_t n, int m, const float *__restrict__ abc32,
+                              const float *__restrict__ coef32, float *__restrict__ out) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * m) return;
+    int64_t i = e / m;
+    int k = (int)(e - i * m);
+    out[e] = fmaf(coef32[16 * k + 2], abc32[2 * n + i], fmaf(coef32[16 * k + 1], abc32[n + i], abc32[i]));
+}
+
+__global__ void k_abc32(int64_t n, const double *__restrict__ abc, float *__restrict__ abc32) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    abc32[i] = (float)(abc[i] / kFourPi);
 }
 
 __global__ void k_interp_apply(int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
@@ -449,43 +537,77 @@ __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const in
     }
 }
 
-template <int DPL, typename T>
-__global__ void __launch_bounds__(256) k_bjacobi(int64_t n, int m, int tm_log2, const int32_t *__restrict__ bof,
-                                                 const int32_t *__restrict__ bmember,
-                                                 const float *__restrict__ Pinv, const T *__restrict__ v,
-                                                 T *__restrict__ z) {
-    const int TM = 1 << tm_log2;
-    const int lane = threadIdx.x & (TM - 1);
-    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
-    if (i >= n) return;
-    const int32_t slot = bof[i];
-    const int64_t blk = slot / kB;
-    T acc[DPL];
-#pragma unroll
-    for (int t = 0; t < DPL; ++t) acc[t] = (T)0;
-    const float *prow = Pinv + (int64_t)slot * kB * m;
-#pragma unroll 4
-    for (int b = 0; b < kB; ++b) {
-        const int32_t j = bmember[blk * kB + b];
-        if (j < 0) continue;
-        const float *pv = prow + (int64_t)b * m;
-        const T *vv = v + (int64_t)j * m;
-#pragma unroll
-        for (int t = 0; t < DPL; ++t) {
-            int kk = lane + t * TM;
-            if (kk < m) acc[t] += (T)pv[kk] * vv[kk];
-        }
+// z = P^{-1} v, one CTA per block of kB points.  The kB input rows v[member]
+// (kB x m values) are staged in shared memory once; the block's inverse
+// (kB x kB x m floats, contiguous) is streamed with 16-byte loads.  Thread
+// (a, c) computes z[member_a][4c .. 4c+3] = sum_b Pinv[a][b][4c..] * v[b][4c..].
+// Requires m % 4 == 0 (the caller falls back to k_bjacobi_scalar otherwise).
+template <typename T>
+__global__ void __launch_bounds__(256) k_bjacobi_blk(int64_t nblk, int m, const int32_t *__restrict__ bmember,
+                                                     const float *__restrict__ Pinv, const T *__restrict__ v,
+                                                     T *__restrict__ z) {
+    extern __shared__ unsigned char smem_raw[];
+    T *vs = reinterpret_cast<T *>(smem_raw);   // [kB][m]
+    const int64_t blk = blockIdx.x;
+    const int mc = m >> 2;                      // float4 chunks per row
+    const int32_t *mem = bmember + blk * kB;
+    for (int q = threadIdx.x; q < kB * m; q += blockDim.x) {
+        int b = q / m, k = q - b * m;
+        int32_t j = mem[b];
+        vs[q] = j >= 0 ? v[(int64_t)j * m + k] : (T)0;
     }
-#pragma unroll
-    for (int t = 0; t < DPL; ++t) {
-        int kk = lane + t * TM;
-        if (kk < m) z[i * m + kk] = acc[t];
+    __syncthreads();
+    const float4 *P4 = reinterpret_cast<const float4 *>(Pinv + blk * (int64_t)kB * kB * m);
+    for (int t = threadIdx.x; t < kB * mc; t += blockDim.x) {
+        const int a = t / mc, c = t - a * mc;
+        const int32_t i = mem[a];
+        if (i < 0) continue;
+        T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+#pragma unroll 4
+        for (int b = 0; b < kB; ++b) {
+            const float4 p = P4[((int64_t)a * kB + b) * mc + c];
+            const T *vb = vs + b * m + 4 * c;
+            acc0 += (T)p.x * vb[0];
+            acc1 += (T)p.y * vb[1];
+            acc2 += (T)p.z * vb[2];
+            acc3 += (T)p.w * vb[3];
+        }
+        T *zo = z + (int64_t)i * m + 4 * c;
+        zo[0] = acc0; zo[1] = acc1; zo[2] = acc2; zo[3] = acc3;
+    }
+}
+
+// general m: one thread per (point of the block, direction)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bjacobi_scalar(int64_t nblk, int m, const int32_t *__restrict__ bmember,
+                                                        const float *__restrict__ Pinv, const T *__restrict__ v,
+                                                        T *__restrict__ z) {
+    extern __shared__ unsigned char smem_raw[];
+    T *vs = reinterpret_cast<T *>(smem_raw);
+    const int64_t blk = blockIdx.x;
+    const int32_t *mem = bmember + blk * kB;
+    for (int q = threadIdx.x; q < kB * m; q += blockDim.x) {
+        int b = q / m, k = q - b * m;
+        int32_t j = mem[b];
+        vs[q] = j >= 0 ? v[(int64_t)j * m + k] : (T)0;
+    }
+    __syncthreads();
+    const float *P = Pinv + blk * (int64_t)kB * kB * m;
+    for (int t = threadIdx.x; t < kB * m; t += blockDim.x) {
+        const int a = t / m, k = t - a * m;
+        const int32_t i = mem[a];
+        if (i < 0) continue;
+        T acc = 0;
+        for (int b = 0; b < kB; ++b) acc += (T)P[((int64_t)a * kB + b) * m + k] * vs[b * m + k];
+        z[(int64_t)i * m + k] = acc;
     }
 }
 
 struct Team {
     int tm_log2, dpl;
 };
+// direction lanes per row: the power of two TM <= 32 that wastes the fewest
+// lanes (TM * DPL >= m, DPL <= 16)
 Team pick_team(int m) {
     Team best{5, (m + 31) / 32};
     double beff = -1.0;
@@ -512,10 +634,9 @@ Team pick_team(int m) {
         default: KERNEL<16><<<grid, 256, 0, s>>>(__VA_ARGS__); break;    \
     }
 
-static int64_t team_grid(int64_t n, const Team &tm) {
-    int64_t threads = n << tm.tm_log2;
-    return (threads + 255) / 256;
-}
+// one warp per row (slot layout) / one team of TM lanes per row
+static int64_t team_grid(int64_t n, const Team &) { return (n * 32 + 255) / 256; }
+static int64_t rowteam_grid(int64_t n, const Team &tm) { return ((n << tm.tm_log2) + 255) / 256; }
 
 static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     const int64_t n = ctx->n, nnz = ctx->nnz;
@@ -531,10 +652,11 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     MLPG_TRY(dalloc(ctx, &ctx->L64, (size_t)nnz * m));
     MLPG_TRY(dalloc(ctx, &ctx->coef, 8 * m));
     MLPG_TRY(dalloc(ctx, &ctx->fcoef, 4 * m));
+    MLPG_TRY(dalloc(ctx, &ctx->coef32, 16 * m));
     MLPG_TRY(dalloc(ctx, &ctx->dinv64, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->dinv32, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->r64, (size_t)n * m));
-    MLPG_TRY(dalloc(ctx, &ctx->abc, 3 * n));
+    MLPG_TRY(dalloc(ctx, &ctx->abc, 5 * n));   // [3][n] FP64 products + [3][n] float copy
     MLPG_TRY(dalloc(ctx, &ctx->Pinv, (size_t)ctx->nblk * kB * kB * m));
     // boundary segment (the face arrays do not depend on dt)
     int *cnt;
@@ -555,7 +677,18 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     k_bfill<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, ctx->col, nnz, Sf, ctx->bptr, ctx->nb,
                                             ctx->bcol, ctx->bval64, ctx->bval32);
     CU_LAUNCH(ctx);
-    k_coef<<<(m + 127) / 128, 128, 0, s>>>(m, ctx->omega, ctx->coef, ctx->fcoef);
+    // list of the rows that have face terms
+    MLPG_TRY(dalloc(ctx, &ctx->brow, n));
+    int *bcount;
+    MLPG_TRY(dalloc(ctx, &bcount, 1));
+    CU(ctx, cudaMemsetAsync(bcount, 0, sizeof(int), s));
+    k_brows<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->bptr, ctx->brow, bcount);
+    CU_LAUNCH(ctx);
+    int nbr = 0;
+    CU(ctx, cudaMemcpyAsync(&nbr, bcount, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    ctx->nbrow = nbr;
+    k_coef<<<(m + 127) / 128, 128, 0, s>>>(m, ctx->omega, ctx->coef, ctx->fcoef, ctx->coef32);
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
@@ -629,8 +762,42 @@ mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *
     int64_t grid = team_grid(ctx->n, tm);
     cudaStream_t s = ctx->stream;
     timing_begin(ctx);
-    DISPATCH_DPL(tm.dpl, k_spmm32, ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->nb, ctx->rowptr, ctx->col,
-                 ctx->A32, ctx->bptr, ctx->bcol, ctx->bval32, ctx->coef, ctx->fcoef, X, B, Y);
+    grid = rowteam_grid(ctx->n, tm);
+    const bool small = ctx->n * (int64_t)ctx->m < (int64_t(1) << 31);
+    const bool exact = (tm.dpl << tm.tm_log2) == ctx->m;
+#define SPMM32_ARGS ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->A32, ctx->coef32, X, B, Y
+#define SPMM32_CASE(D)                                                                         \
+    case D:                                                                                    \
+        if (exact && small) k_spmm32<D, true, int32_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);      \
+        else if (small) k_spmm32<D, false, int32_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);         \
+        else k_spmm32<D, false, int64_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);                    \
+        break;
+    switch (tm.dpl) {
+        SPMM32_CASE(1) SPMM32_CASE(2) SPMM32_CASE(3) SPMM32_CASE(4) SPMM32_CASE(5) SPMM32_CASE(6)
+        SPMM32_CASE(7) SPMM32_CASE(8) SPMM32_CASE(9) SPMM32_CASE(10) SPMM32_CASE(11) SPMM32_CASE(12)
+        default:
+            if (small) k_spmm32<16, false, int32_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);
+            else k_spmm32<16, false, int64_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);
+            break;
+    }
+    CU_LAUNCH(ctx);
+    if (ctx->nbrow > 0) {
+        int64_t gb = team_grid(ctx->nbrow, tm);
+        float sign = B ? -1.0f : 1.0f;
+#define FACE_CASE(D) \
+    case D: k_faces32<D><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr, ctx->bcol, \
+                                          ctx->bval32, ctx->coef32, X, sign, Y); break;
+        switch (tm.dpl) {
+            FACE_CASE(1) FACE_CASE(2) FACE_CASE(3) FACE_CASE(4) FACE_CASE(5) FACE_CASE(6) FACE_CASE(8)
+            case 7: k_faces32<8><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr,
+                                                    ctx->bcol, ctx->bval32, ctx->coef32, X, sign, Y); break;
+            default: k_faces32<16><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr,
+                                                       ctx->bcol, ctx->bval32, ctx->coef32, X, sign, Y); break;
+        }
+#undef FACE_CASE
+    }
+#undef SPMM32_CASE
+#undef SPMM32_ARGS
     timing_end(ctx);
     CU_LAUNCH(ctx);
     return MLPG_OK;
@@ -643,6 +810,7 @@ mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F) {
     Team tm = pick_team(ctx->m);
     int64_t grid = team_grid(ctx->n, tm);
     cudaStream_t s = ctx->stream;
+    grid = rowteam_grid(ctx->n, tm);
     DISPATCH_DPL(tm.dpl, k_rhs64, ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->T64,
                  ctx->coef, Psi_prev, ctx->r64, F);
     CU_LAUNCH(ctx);
@@ -656,7 +824,14 @@ mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out) {
     k_ms_spmv<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->nnz, ctx->rowptr, ctx->col, ctx->S64, phi, ctx->abc);
     CU_LAUNCH(ctx);
     int64_t nm = n * ctx->m;
-    k_ms_expand<T><<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, ctx->abc, ctx->coef, out);
+    if constexpr (sizeof(T) == 4) {
+        float *abc32 = (float *)(ctx->abc + 3 * n);
+        k_abc32<<<(3 * n + 255) / 256, 256, 0, s>>>(n, ctx->abc, abc32);
+        CU_LAUNCH(ctx);
+        k_ms_expand32<<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, abc32, ctx->coef32, (float *)out);
+    } else {
+        k_ms_expand<T><<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, ctx->abc, ctx->coef, out);
+    }
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
@@ -665,18 +840,17 @@ template mlpg_status apply_MS<float>(mlpg_ctx *, const double *, float *);
 
 template <typename T>
 mlpg_status apply_prec(mlpg_ctx *ctx, const T *v, T *z) {
-    Team tm = pick_team(ctx->m);
-    int64_t grid = team_grid(ctx->n, tm);
-    cudaStream_t s = ctx->stream;
-    switch (tm.dpl) {
-        case 1: k_bjacobi<1, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
-        case 2: k_bjacobi<2, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
-        case 3: k_bjacobi<3, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
-        case 4: k_bjacobi<4, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
-        case 5: case 6: k_bjacobi<6, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
-        case 7: case 8: k_bjacobi<8, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
-        default: k_bjacobi<16, T><<<grid, 256, 0, s>>>(ctx->n, ctx->m, tm.tm_log2, ctx->bof, ctx->bmember, ctx->Pinv, v, z); break;
+    const size_t smem = sizeof(T) * kB * ctx->m;
+    if (smem > 200 * 1024) return set_err(ctx, MLPG_ERR_ARG, "too many directions for the block preconditioner");
+    if (smem > 48 * 1024) {
+        CU(ctx, cudaFuncSetAttribute(k_bjacobi_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CU(ctx, cudaFuncSetAttribute(k_bjacobi_scalar<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
+    if ((ctx->m & 3) == 0)
+        k_bjacobi_blk<T><<<(unsigned)ctx->nblk, 256, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember, ctx->Pinv, v, z);
+    else
+        k_bjacobi_scalar<T><<<(unsigned)ctx->nblk, 256, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember, ctx->Pinv,
+                                                                              v, z);
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
