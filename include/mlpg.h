@@ -172,6 +172,36 @@ mlpg_status mlpg_get_forms(const mlpg_ctx *ctx, double *mats, double *vecs);
  * arrays of `precision` (MLPG_FP64: double, MLPG_MIXED: float). */
 mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void *X, void *Y);
 
+/* ---- allocation-free helper ----------------------------------------------- */
+
+/* Largest n accepted by mlpg_overlap_counts_noalloc. */
+#define MLPG_NOALLOC_MAX_POINTS 262144
+
+/* Row sizes of the overlap pattern, counts[i] = #{j : |x_i - x_j| < R_i + R_j},
+ * for callers that cannot allocate device memory when they need them: code
+ * running while a stream is captured into a CUDA graph, code living inside a
+ * device memory budget fixed at start-up, real-time loops that must not touch
+ * the allocator.  With the counts such a caller can size its own buffers.
+ * The paper has no counterpart of this call (it is a service of this library);
+ * the counts equal the row lengths of the pattern mlpg_integrate builds.
+ *   points[n*dim], kernel_extent[n]: device arrays (finite, extents > 0,
+ *                                    points inside [lo, hi])
+ *   lo[dim], hi[dim]:                host arrays, the box
+ *   counts[n]:                       device output (int32)
+ *   stream:                          cudaStream_t, NULL = legacy default stream
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
+ * scratch is one static device array of about 2.8 MB that every GPU loading
+ * this library holds until the process exits; n > MLPG_NOALLOC_MAX_POINTS
+ * returns MLPG_ERR_ARG.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the one array: calls
+ * that overlap on the GPU (different streams, or host threads without
+ * ordering) race and give wrong counts; order them on one stream.  Work is
+ * queued on `stream` and the call returns without waiting. */
+mlpg_status mlpg_overlap_counts_noalloc(int dim, int64_t n, const double *points,
+                                        const double *kernel_extent, const double *lo,
+                                        const double *hi, int32_t *counts, void *stream);
+
 /* Last error message of this context ("" when none). */
 const char *mlpg_last_error(const mlpg_ctx *ctx);
 

@@ -93,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "mlpg_n_vectors": (ctypes.c_int, [ctypes.c_int]),
         "mlpg_get_forms": (i32, [_P, _P, _P]),
         "mlpg_apply_L_dev": (i32, [_P, dbl, ctypes.c_int, _P, _P]),
+        "mlpg_overlap_counts_noalloc": (i32, [ctypes.c_int, i64, _P, _P, _P, _P, _P, _P]),
         "mlpg_last_error": (ctypes.c_char_p, [_P]),
         "mlpg_destroy": (None, [_P]),
     }
@@ -240,6 +241,16 @@ def mlpg_get_forms(ctx, n, nnz, dim=2):
 
 def mlpg_apply_L_dev(ctx, dt, precision, x_ptr, y_ptr):
     _check(ctx, load_library().mlpg_apply_L_dev(ctx, dt, precision, x_ptr, y_ptr))
+
+
+def mlpg_overlap_counts_noalloc(dim, n, points_ptr, extent_ptr, lo, hi, counts_ptr, stream=None):
+    """Row sizes of the overlap pattern into a device int32 buffer, without any
+    device allocation (device pointers in and out; lo/hi are host sequences).
+    Returns the status code (0 on success); the work is queued on `stream`."""
+    lo_a = _arr(list(lo)[:dim])
+    hi_a = _arr(list(hi)[:dim])
+    return load_library().mlpg_overlap_counts_noalloc(dim, n, points_ptr, extent_ptr, _ptr(lo_a), _ptr(hi_a),
+                                                      counts_ptr, stream)
 
 
 def mlpg_last_error(ctx):
