@@ -246,6 +246,7 @@ mlpg_status mlpg_set_initial(mlpg_ctx *ctx, const double *psi0) {
     k_phi_from_psi<<<(ctx->n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n, ctx->m, ctx->w, ctx->Psi, ctx->Phi);
     CU_LAUNCH(ctx);
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->nhist = 0;   // a new state: no history for the initial guess
     return MLPG_OK;
 }
 

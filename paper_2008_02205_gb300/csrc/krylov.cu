@@ -331,6 +331,20 @@ __global__ void k_combine(int64_t n, int M, int kmax, const T *__restrict__ V, i
     u[e] = (T)s;
 }
 
+// acc += sum_{l < kcol[0]} y_l bank_l   (single system: the outer solve)
+template <typename T>
+__global__ void k_bank_combine(int64_t N, int kmax, const T *__restrict__ bank,
+                               const typename Arith<T>::type *__restrict__ y, const int *__restrict__ kcol,
+                               T *__restrict__ acc) {
+    using A = typename Arith<T>::type;
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int k = min(kcol[0], kmax);
+    A s = (A)acc[e];
+    for (int l = 0; l < k; ++l) s += y[l] * (A)bank[(int64_t)l * N + e];
+    acc[e] = (T)s;
+}
+
 template <typename T>
 __global__ void k_axpy1(int64_t N, const T *__restrict__ u, T *__restrict__ x) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -356,6 +370,18 @@ template <typename Ti, typename To>
 __global__ void k_convert(int64_t N, const Ti *__restrict__ a, To *__restrict__ b) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e < N) b[e] = (To)a[e];
+}
+
+// Initial guess of a step from the last states, in place:
+//   psi <- a psi + b h1 + c h2   (psi = Psi^{n-1}, h1 = Psi^{n-2}, h2 = Psi^{n-3})
+// and h2 <- Psi^{n-1} (h2 becomes the newest history entry).
+__global__ void k_extrap(int64_t N, double a, double b, double c, double *__restrict__ psi,
+                         const double *__restrict__ h1, double *__restrict__ h2) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const double p = psi[e];
+    psi[e] = a * p + b * h1[e] + c * h2[e];
+    h2[e] = p;
 }
 
 // c = a + b (mixed types; c may alias a)
@@ -434,13 +460,16 @@ template <typename T>
 using ApplyFn = std::function<mlpg_status(const T *X, const T *B, T *Y)>;
 template <typename T>
 using PrecFn = std::function<mlpg_status(const T *v, T *z)>;
+// called after each cycle's least-squares solve: y (FP64 and FP32 copies), kcol
+using CycleFn = std::function<mlpg_status(const double *y, const float *y32, const int *kcol, int kmax)>;
 
 // Solve A x = b for all M systems, right preconditioned by P (identity when
 // empty); x holds the initial guess.  Returns the summed iteration count in
 // *iters and MLPG_ERR_NOT_CONVERGED on the cap.
 template <typename T>
 static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, const PrecFn<T> &P, const T *b,
-                               T *x, double tol, int max_its, int check_every, int64_t *iters) {
+                               T *x, double tol, int max_its, int check_every, int64_t *iters,
+                               const CycleFn &on_cycle = CycleFn(), int *slot = nullptr) {
     const int64_t n = G.n, N = n * G.M;
     const int M = G.M, R = G.R;
     const int64_t vs = N;
@@ -469,6 +498,7 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
                                                     0.0, 1, G.d_active_count);
             CU_LAUNCH(ctx);
         }
+        if (slot) *slot = cycle == 0 ? -1 : -2;   // -1: first residual, -2: later residuals
         MLPG_TRY(A(x, b, G.V));  // r = b - A x -> V_0
         MLPG_TRY(norm2(G.V));
         CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
@@ -489,6 +519,7 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         int jlast = 0;
         for (int j = 0; j < R; ++j) {
             T *w = G.V + (j + 1) * vs;
+            if (slot) *slot = j;                      // operator applied to basis vector j
             MLPG_TRY(A(z, nullptr, w));
             {
                 // CGS2 in three fused passes over V_0..V_j
@@ -530,6 +561,7 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         }
         k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y, G.y32);
         CU_LAUNCH(ctx);
+        if (on_cycle) MLPG_TRY(on_cycle(G.y, G.y32, G.kcol, jlast + 1));
         k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, y_of<T>(G), G.kcol, G.W);
         CU_LAUNCH(ctx);
         const T *u = precond(G.W, G.Z);
@@ -602,6 +634,21 @@ static mlpg_status ensure_step_buffers(mlpg_ctx *ctx) {
     return MLPG_OK;
 }
 
+template <typename T>
+static mlpg_status outer_bank(mlpg_ctx *ctx, int R, T **bank, T **xacc) {
+    const size_t N = (size_t)ctx->n * ctx->m;
+    void **slotp = sizeof(T) == 8 ? &ctx->bank64 : &ctx->bank32;
+    if (!*slotp) {
+        T *p = nullptr;
+        MLPG_TRY(dalloc(ctx, &p, (size_t)(R + 1) * N));
+        *slotp = p;
+    }
+    T *base = static_cast<T *>(*slotp);
+    *bank = base;
+    *xacc = base + (size_t)R * N;
+    return MLPG_OK;
+}
+
 // Nested solve of (L - MS D) Psi = f (Sec. 4.2): first flight, GMRES on Phi,
 // recovery.  f and Psi are FP64 [n][m]; inner solves run in T.  Phi_io holds
 // the initial guess of Phi on entry (may be null) and the result on exit.
@@ -631,24 +678,40 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     MLPG_TRY(gmres_alloc(ctx, ctx->gout, n, 1, ctx->opt.outer_restart));
     if (Phi_io) CU(ctx, cudaMemcpyAsync(phi, Phi_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else CU(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, s));
-    ApplyFn<double> A = [ctx, rhs, x, d, n, s](const double *X, const double *B, double *Y) -> mlpg_status {
+    // Each operator apply solves x = L^{-1} MS v for one outer basis vector v.
+    // Those solutions are kept (bank) so that L^{-1} MS Phi, needed for the
+    // angular recovery Psi = L^{-1} MS Phi + b_psi, is the same combination of
+    // them as Phi is of the basis: no separate recovery solve.
+    const int Rout = ctx->opt.outer_restart;
+    T *bank, *xacc;
+    MLPG_TRY(outer_bank<T>(ctx, Rout, &bank, &xacc));
+    int slot = -1;
+    ApplyFn<double> A = [ctx, rhs, x, d, n, N, s, bank, xacc, &slot](const double *X, const double *B,
+                                                                    double *Y) -> mlpg_status {
+        T *xt = slot >= 0 ? bank + (int64_t)slot * N : (slot == -1 ? xacc : x);
         MLPG_TRY(apply_MS<T>(ctx, X, rhs));
-        MLPG_TRY(inner_solve<T>(ctx, rhs, x, ctx->cur_inner_tol));
-        k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, x, d);
+        MLPG_TRY(inner_solve<T>(ctx, rhs, xt, ctx->cur_inner_tol));
+        k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, xt, d);
         CU_LAUNCH(ctx);
         k_outer_combine<<<nblk(n), kBlock, 0, s>>>(n, X, d, B, Y);
+        CU_LAUNCH(ctx);
+        return MLPG_OK;
+    };
+    CycleFn on_cycle = [ctx, N, s, bank, xacc](const double *y, const float *y32, const int *kcol,
+                                                int kmax) -> mlpg_status {
+        const typename Arith<T>::type *yy;
+        if constexpr (sizeof(T) == 8) yy = y; else yy = y32;
+        k_bank_combine<T><<<nblk(N), kBlock, 0, s>>>(N, kmax, bank, yy, kcol, xacc);
         CU_LAUNCH(ctx);
         return MLPG_OK;
     };
     ctx->cur_inner_tol = inner_tol;
     int64_t oits = 0;
     MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol, ctx->opt.max_outer, 1,
-                                 &oits));
+                                 &oits, on_cycle, &slot));
     ctx->st.last_outer_iters += (int32_t)oits;
-    // recovery Psi = L^{-1} MS Phi + b_psi
-    MLPG_TRY(apply_MS<T>(ctx, phi, rhs));
-    MLPG_TRY(inner_solve<T>(ctx, rhs, x, inner_tol));
-    k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, x, bpsi, Psi_out);
+    // Psi = L^{-1} MS Phi + b_psi
+    k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, xacc, bpsi, Psi_out);
     CU_LAUNCH(ctx);
     if (Phi_io) CU(ctx, cudaMemcpyAsync(Phi_io, phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     return MLPG_OK;
@@ -661,6 +724,16 @@ static mlpg_status global_norm(mlpg_ctx *ctx, const double *a, int64_t N, double
     k_reduce<<<1, 32, 0, ctx->stream>>>(1, 1, (int)G, ctx->red, ctx->red + 2048);
     CU_LAUNCH(ctx);
     CU(ctx, cudaMemcpyAsync(out_host_slot, ctx->red + 2048, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    return MLPG_OK;
+}
+
+static mlpg_status ensure_history(mlpg_ctx *ctx) {
+    if (!ctx->hist[0]) {
+        const size_t N = (size_t)ctx->n * ctx->m;
+        MLPG_TRY(dalloc(ctx, &ctx->hist[0], N));
+        MLPG_TRY(dalloc(ctx, &ctx->hist[1], N));
+        ctx->nhist = 0;
+    }
     return MLPG_OK;
 }
 
@@ -715,7 +788,25 @@ mlpg_status step_mixed(mlpg_ctx *ctx, double dt) {
     cudaStream_t s = ctx->stream;
     MLPG_TRY(rhs_T(ctx, ctx->Psi, ctx->f64));
     MLPG_TRY(global_norm(ctx, ctx->f64, N, ctx->h_red + 1));
-    // Psi^{(0)} = Psi^{n-1}; refine Psi += (L - MS D)^{-1}_{FP32} R
+    // Initial guess: polynomial extrapolation of the last states (the
+    // converged result does not depend on it; a close guess saves sweeps).
+    MLPG_TRY(ensure_history(ctx));
+    {
+        double *h1 = ctx->hist[0], *h2 = ctx->hist[1];   // Psi^{n-2}, Psi^{n-3} (when valid)
+        const int nh = ctx->nhist;
+        if (nh == 0) {
+            CU(ctx, cudaMemcpyAsync(h2, ctx->Psi, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        } else {
+            // linear (one history state) or quadratic (two) extrapolation
+            const double a = nh >= 2 ? 3.0 : 2.0, b = nh >= 2 ? -3.0 : -1.0, c = nh >= 2 ? 1.0 : 0.0;
+            k_extrap<<<nblk(N), kBlock, 0, s>>>(N, a, b, c, ctx->Psi, h1, h2);
+            CU_LAUNCH(ctx);
+        }
+        ctx->hist[0] = h2;   // Psi^{n-1}
+        ctx->hist[1] = h1;   // Psi^{n-2}
+        ctx->nhist = nh < 2 ? nh + 1 : 2;
+    }
+    // refine Psi += (L - MS D)^{-1}_{FP32} R
     double *phi_c = ctx->nvec + 3 * n;
     int k = 0;
     double rel = 0.0;
