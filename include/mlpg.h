@@ -58,7 +58,7 @@ typedef struct {
     int max_outer;         /* outer iteration cap per solve; default 500 */
     double refine_tol;     /* MLPG_MIXED: FP64 step residual ||R|| <= tol ||f||; default 1e-11 */
     int max_refine;        /* MLPG_MIXED: refinement sweeps per step; default 12 */
-    double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-5 */
+    double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-2 */
     int check_every;       /* inner GMRES: host convergence check interval (steps); default 4 */
     int mixed_restart;     /* MLPG_MIXED: restart length of the FP32 inner GMRES (<= 32); default 10 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */

@@ -204,7 +204,7 @@ void mlpg_default_options(mlpg_options *o) {
     o->max_outer = 500;
     o->refine_tol = 1e-11;
     o->max_refine = 12;
-    o->mixed_inner_tol = 1e-5;
+    o->mixed_inner_tol = 1e-2;
     o->check_every = 4;
     o->mixed_restart = 10;
     o->stream = nullptr;

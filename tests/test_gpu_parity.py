@@ -210,3 +210,45 @@ def test_error_paths():
         with pytest.raises(pkg.MlpgError) as e:
             t3.step(0.01)
         assert e.value.status == -7
+
+
+@pytest.mark.slow
+def test_full_size_256_two_region_S8():
+    """The benchmark workload (256x256 jittered points, S8, two-region sigma,
+    dt 0.005) in the benchmark's launch configuration (mixed precision,
+    default options): pattern bit-exact, volumes and every integrated form
+    against the oracle, and one backward-Euler step checked through a property
+    that holds at any size: the FP64 step residual ||f - (L - MS D) Psi|| / ||f||
+    evaluated with the oracle's own operators."""
+    import scipy.sparse as sp
+    prob = mi.two_region_2d()
+    disc = O.Discretization(prob.x, prob.R)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED) as tp:
+        tp.integrate().assemble()
+        rowptr, col = tp.neighbors()
+        assert np.array_equal(rowptr, disc.rowptr) and np.array_equal(col, disc.col)
+        assert np.abs(tp.volumes() - disc.V).max() <= 1e-13 * disc.V.max()
+        mats, vecs = tp.forms()
+        d = 2
+        ref_m = np.concatenate([F["M0"][None], F["Mt"][None], F["Ms"][None], F["G"], F["Gt"], F["Gs"],
+                                F["K"].reshape(d * d, -1), F["S"]])
+        for k in range(ref_m.shape[0]):
+            assert np.abs(mats[k] - ref_m[k]).max() <= 1e-12 * np.abs(ref_m[k]).max(), k
+        ref_v = np.concatenate([F["Q0"][None], F["Q"], F["B"]])
+        for k in range(ref_v.shape[0]):
+            assert np.abs(vecs[k] - ref_v[k]).max() <= 1e-12 * max(np.abs(ref_v[k]).max(), 1e-300), k
+        tp.step(prob.dt)
+        Psi = tp.state().T            # [m, n]
+        st = tp.stats()
+    tr = O.Transport(disc, F, prob.omega, prob.w)
+    kap = 1.0 / prob.dt
+    res2, f2 = 0.0, 0.0
+    Phi = tr.w @ Psi
+    for m in range(tr.M):
+        f = tr.T_matrix(m, kap) @ np.zeros(disc.n) + tr.r_vector(m)    # Psi^0 = 0
+        r = f - tr.L_matrix(m, kap) @ Psi[m] + tr.MS_matrix(m) @ Phi
+        res2 += r @ r
+        f2 += f @ f
+    assert np.sqrt(res2 / f2) < 1e-9
+    assert st["last_residual"] < 1e-10
