@@ -44,6 +44,9 @@ def _args():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end solves")
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply"],
+                    help="solve: whole solves (the benchmark); apply: only the batched L-apply of the "
+                         "workload, timed per launch (used for kernel profiles)")
     ap.add_argument("--be-steps", type=int, default=None,
                     help="backward-Euler steps per solve (default: the workload's 20; profiling runs use fewer)")
     return ap.parse_args()
@@ -112,6 +115,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+PROFILE = os.path.join(ROOT, "profiles", "k_spmm32-2d-two-region-256x256-S8.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2008_02205_gb300", "csrc", "operators.cu")
+
+
+def _traffic():
+    """DRAM bytes per launch of the FP32 L-apply from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    import hashlib
+    try:
+        txt = open(PROFILE).read()
+        src = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+            k, v = line.split(":", 1)
+            vals[k.strip(" -`*")] = v.strip(" `*")
+    if vals.get("source_sha256") != src:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -162,6 +191,46 @@ def _reference(args):
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank):
+    """Time the batched L-apply alone on the workload's operators (one launch
+    per step, CUDA events on the library stream); used for kernel profiles."""
+    import torch
+    o = pkg.mlpg_default_options(**opts)
+    ctx = pkg.mlpg_create_dev(o, prob.n, prob.m, dv["x"].data_ptr(), dv["R"].data_ptr(), dv["om"].data_ptr(),
+                              dv["w"].data_ptr(), dv["st"].data_ptr(), dv["ss"].data_ptr(), dv["q"].data_ptr())
+    try:
+        pkg.mlpg_integrate(ctx)
+        pkg.mlpg_assemble(ctx)
+        dt = torch.float32 if prec == pkg.MLPG_MIXED else torch.float64
+        X = torch.rand(prob.n, prob.m, device=stream.device, dtype=dt)
+        Y = torch.empty_like(X)
+        for _ in range(args.warmup):
+            pkg.mlpg_apply_L_dev(ctx, prob.dt, prec, X.data_ptr(), Y.data_ptr())
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pkg.mlpg_apply_L_dev(ctx, prob.dt, prec, X.data_ptr(), Y.data_ptr())
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        st = pkg.mlpg_get_stats(ctx)
+    finally:
+        pkg.mlpg_destroy(ctx)
+    us = 1e3 * statistics.median(times)
+    hbm, kind = _peaks()
+    gbs = st["spmm_bytes"] / (us * 1e-6) / 1e9
+    if rank == 0:
+        print(json.dumps({"metric": "batched L-apply", "value": us, "unit": "us/launch", "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+                          "dtype": "f32" if prec == pkg.MLPG_MIXED else "f64",
+                          "config": {"workload": WORKLOAD, "mode": "apply"},
+                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                       "frac": gbs / hbm, "peak_kind": kind,
+                                       "bytes_per_launch": st["spmm_bytes"]}}))
 
 
 def main():
@@ -221,6 +290,9 @@ def main():
         finally:
             pkg.mlpg_destroy(ctx)
 
+    if args.mode == "apply":
+        _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank)
+        return
     for _ in range(args.warmup):
         solve_device()
     torch.cuda.synchronize()
@@ -280,8 +352,8 @@ def main():
         achieved = stats["spmm_bytes"] / per_launch_s / 1e9
         roof = {"kernel": "k_spmm32 (batched L-apply)" if prec == pkg.MLPG_MIXED else "k_spmm64 (batched L-apply)",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": stats["spmm_bytes"],
-                "us_per_launch": per_launch_s * 1e6}
+                "traffic": _traffic() if prec == pkg.MLPG_MIXED else None, "peak_kind": peak_kind,
+                "bytes_per_launch": stats["spmm_bytes"], "us_per_launch": per_launch_s * 1e6}
     lat = sorted(per)
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
