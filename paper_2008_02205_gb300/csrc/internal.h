@@ -204,8 +204,9 @@ mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F);
 template <typename T>
 mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out);
 mlpg_status interp_flux(mlpg_ctx *ctx, double *out_dev, int kind);
+// z = P^{-1} v (block-Jacobi); with sc != null, v is first scaled in place by sc[direction]
 template <typename T>
-mlpg_status apply_prec(mlpg_ctx *ctx, const T *v, T *z);
+mlpg_status apply_prec(mlpg_ctx *ctx, T *v, T *z, const double *sc);
 mlpg_status build_blocks(mlpg_ctx *ctx);
 void harvest_timing(mlpg_ctx *ctx);
 }  // namespace mlpg

@@ -50,7 +50,7 @@ int grid_rows(int64_t n, const Map2 &mp, int nl) {
     return (int)g;
 }
 
-// partial[(l * G + block) * M + m] = sum over this block's rows of V_l[i][m] * w[i][m]
+// partial[(l * M + m) * G + block] = sum over this block's rows of V_l[i][m] * w[i][m]
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_dots(int64_t n, int M, int MB, int RB, const T *__restrict__ V,
                                                  int64_t vstride, const T *__restrict__ w,
@@ -77,20 +77,32 @@ __global__ void __launch_bounds__(kBlock) k_dots(int64_t n, int M, int MB, int R
     if (r == 0 && m < M) {
         double s = 0.0;
         for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
-        partial[((int64_t)l * G + blockIdx.x) * M + m] = s;
+        partial[((int64_t)l * M + m) * G + blockIdx.x] = s;
     }
 }
 
-// out[l * M + m] = sum_g partial[(l * G + g) * M + m]; one warp per output,
-// fixed lane order and shuffle tree: deterministic.
+// out[l * M + m] = sum_g partial[(l * M + m) * G + g]; one warp per output
+// (contiguous partials), fixed lane order and shuffle tree: deterministic.
+__device__ __forceinline__ double warp_sum_partials(const double *__restrict__ part, int G, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int g = lane;
+    for (; g + 96 < G; g += 128) {
+        s0 += part[g];
+        s1 += part[g + 32];
+        s2 += part[g + 64];
+        s3 += part[g + 96];
+    }
+    for (; g < G; g += 32) s0 += part[g];
+    double s = (s0 + s1) + (s2 + s3);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
 __global__ void k_reduce(int M, int nl, int G, const double *__restrict__ partial, double *__restrict__ out) {
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= (int64_t)M * nl) return;
-    const int l = (int)(wid / M), m = (int)(wid - (int64_t)l * M);
-    double s = 0.0;
-    for (int g = lane; g < G; g += 32) s += partial[((int64_t)l * G + g) * M + m];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const double s = warp_sum_partials(partial + wid * G, G, lane);
     if (lane == 0) out[wid] = s;
 }
 
@@ -141,7 +153,7 @@ __global__ void __launch_bounds__(kBlock) k_update_norm(int64_t n, int M, int MB
     if (r == 0 && m < M) {
         double s = 0.0;
         for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
-        partial[(int64_t)blockIdx.x * M + m] = s;
+        partial[(int64_t)m * G + blockIdx.x] = s;
     }
 }
 
@@ -151,7 +163,7 @@ __global__ void __launch_bounds__(kBlock) k_update_norm(int64_t n, int M, int MB
 //   MODE 0:  h_l = V_l . w
 //   MODE 1:  w <- w - sum_l hin_l V_l, then h_l = V_l . w
 //   MODE 2:  w <- w - sum_l hin_l V_l, then ||w||^2
-// Block sums go to partial[(l * G + block) * M + m].
+// Block sums go to partial[(l * M + m) * G + block].
 template <typename T, int MAXL, int MODE>
 __global__ void __launch_bounds__(kBlock) k_cgs(int64_t n, int M, int MB, int RB, int nl,
                                                 const T *__restrict__ V, int64_t vs,
@@ -198,7 +210,7 @@ __global__ void __launch_bounds__(kBlock) k_cgs(int64_t n, int M, int MB, int RB
             if (r == 0 && m < M) {
                 double s = 0.0;
                 for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
-                partial[((int64_t)l * G + blockIdx.x) * M + m] = s;
+                partial[((int64_t)l * M + m) * G + blockIdx.x] = s;
             }
             __syncthreads();
         }
@@ -234,19 +246,23 @@ __global__ void k_start(int M, int R, const double *__restrict__ nrm2, double *_
 }
 
 // Column j of the Hessenberg matrix, Givens rotations, residual estimate.
-__global__ void k_givens(int M, int R, int j, const double *__restrict__ h1, const double *__restrict__ h2,
-                         const double *__restrict__ nrm2, double *__restrict__ H, double *__restrict__ cs,
-                         double *__restrict__ sn, double *__restrict__ g, double *__restrict__ sc,
-                         int *__restrict__ active, int *__restrict__ kcol, int *__restrict__ its,
-                         double *__restrict__ resid, const double *__restrict__ bnorm, double tol,
-                         int *__restrict__ count) {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per system: the warp first sums the G norm partials of ||w||^2.
+__global__ void k_givens(int M, int R, int j, int G, const double *__restrict__ partial,
+                         const double *__restrict__ h1, const double *__restrict__ h2, double *__restrict__ H,
+                         double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
+                         double *__restrict__ sc, int *__restrict__ active, int *__restrict__ kcol,
+                         int *__restrict__ its, double *__restrict__ resid, const double *__restrict__ bnorm,
+                         double tol, int *__restrict__ count) {
+    const int m = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
     if (m >= M) return;
     if (!active[m]) {
-        sc[m] = 0.0;
+        if (lane == 0) sc[m] = 0.0;
         return;
     }
-    double hn = sqrt(nrm2[m]);
+    const double nrm2 = warp_sum_partials(partial + (int64_t)m * G, G, lane);
+    if (lane != 0) return;
+    double hn = sqrt(nrm2);
     double *Hm = H + (int64_t)m * (R + 1) * R;  // Hm[row * R + col]
     for (int l = 0; l <= j; ++l) Hm[l * R + j] = h1[l * M + m] + h2[l * M + m];
     Hm[(j + 1) * R + j] = hn;
@@ -459,7 +475,7 @@ static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int
 template <typename T>
 using ApplyFn = std::function<mlpg_status(const T *X, const T *B, T *Y)>;
 template <typename T>
-using PrecFn = std::function<mlpg_status(const T *v, T *z)>;
+using PrecFn = std::function<mlpg_status(T *v, T *z, const double *sc)>;  // z = P^{-1} (v *= sc)
 // called after each cycle's least-squares solve: y (FP64 and FP32 copies), kcol
 using CycleFn = std::function<mlpg_status(const double *y, const float *y32, const int *kcol, int kmax)>;
 
@@ -469,7 +485,7 @@ using CycleFn = std::function<mlpg_status(const double *y, const float *y32, con
 template <typename T>
 static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, const PrecFn<T> &P, const T *b,
                                T *x, double tol, int max_its, int check_every, int64_t *iters,
-                               const CycleFn &on_cycle = CycleFn(), int *slot = nullptr) {
+                               const CycleFn &on_cycle = CycleFn(), int *slot = nullptr, bool x_zero = false) {
     const int64_t n = G.n, N = n * G.M;
     const int M = G.M, R = G.R;
     const int64_t vs = N;
@@ -485,25 +501,34 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         CU_LAUNCH(ctx);
         return MLPG_OK;
     };
-    auto precond = [&](const T *v, T *z) -> const T * {
-        if (!P) return v;
-        return P(v, z) == MLPG_OK ? z : nullptr;
+    // normalise v by sc (when given) and precondition: returns the vector to apply A to
+    auto precond = [&](T *v, T *z, const double *sc) -> const T * {
+        if (!P) {
+            if (sc) k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, v, sc);
+            return cudaGetLastError() == cudaSuccess ? v : nullptr;
+        }
+        return P(v, z, sc) == MLPG_OK ? z : nullptr;
     };
     int64_t total = 0;
     for (int cycle = 0;; ++cycle) {
-        if (cycle == 0) {
+        const bool first_zero = cycle == 0 && x_zero;   // r = b: no operator apply needed
+        if (cycle == 0 && !x_zero) {
             MLPG_TRY(norm2(b));
             CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
             k_start<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.nrm2, G.bnorm, G.g, G.beta, G.active, G.kcol, G.resid,
                                                     0.0, 1, G.d_active_count);
             CU_LAUNCH(ctx);
         }
-        if (slot) *slot = cycle == 0 ? -1 : -2;   // -1: first residual, -2: later residuals
-        MLPG_TRY(A(x, b, G.V));  // r = b - A x -> V_0
+        if (first_zero) {
+            CU(ctx, cudaMemcpyAsync(G.V, b, sizeof(T) * N, cudaMemcpyDeviceToDevice, s));
+        } else {
+            if (slot) *slot = cycle == 0 ? -1 : -2;   // -1: first residual, -2: later residuals
+            MLPG_TRY(A(x, b, G.V));  // r = b - A x -> V_0
+        }
         MLPG_TRY(norm2(G.V));
         CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
         k_start<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.nrm2, G.bnorm, G.g, G.beta, G.active, G.kcol, G.resid, tol,
-                                                0, G.d_active_count);
+                                                first_zero ? 1 : 0, G.d_active_count);
         CU_LAUNCH(ctx);
         CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
@@ -512,15 +537,14 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
             *iters = total;
             return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
         }
-        k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, G.V, G.beta);
-        CU_LAUNCH(ctx);
-        const T *z = precond(G.V, G.Z);
+        const T *z = precond(G.V, G.Z, G.beta);
         if (!z) return MLPG_ERR_CUDA;
         int jlast = 0;
         for (int j = 0; j < R; ++j) {
             T *w = G.V + (j + 1) * vs;
             if (slot) *slot = j;                      // operator applied to basis vector j
             MLPG_TRY(A(z, nullptr, w));
+            int gnorm = 0;
             {
                 // CGS2 in three fused passes over V_0..V_j
                 // fewer, longer-running blocks as the basis grows (bounded partial sums)
@@ -539,13 +563,11 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
                 CU_LAUNCH(ctx);
                 launch_cgs<T, 2>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.h2, w, G.partial);
                 CU_LAUNCH(ctx);
-                k_reduce<<<wblk, kBlock, 0, s>>>(M, 1, g1, G.partial, G.nrm2);
-                CU_LAUNCH(ctx);
+                gnorm = g1;   // the norm partials are reduced inside k_givens
             }
             CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
-            k_givens<<<(M + 127) / 128, 128, 0, s>>>(M, R, j, G.h, G.h2, G.nrm2, G.H, G.cs, G.sn, G.g, G.beta,
-                                                     G.active, G.kcol, G.its, G.resid, G.bnorm, tol,
-                                                     G.d_active_count);
+            k_givens<<<wblk, kBlock, 0, s>>>(M, R, j, gnorm, G.partial, G.h, G.h2, G.H, G.cs, G.sn, G.g, G.beta,
+                                             G.active, G.kcol, G.its, G.resid, G.bnorm, tol, G.d_active_count);
             CU_LAUNCH(ctx);
             jlast = j;
             bool check = (j + 1) % check_every == 0 || j + 1 == R;
@@ -554,9 +576,7 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
                 CU(ctx, cudaStreamSynchronize(s));
                 if (*G.h_active == 0) break;
             }
-            k_scale<T><<<nblk(N), kBlock, 0, s>>>(n, M, w, G.beta);
-            CU_LAUNCH(ctx);
-            z = precond(w, G.Z);
+            z = precond(w, G.Z, G.beta);
             if (!z) return MLPG_ERR_CUDA;
         }
         k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y, G.y32);
@@ -564,7 +584,7 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         if (on_cycle) MLPG_TRY(on_cycle(G.y, G.y32, G.kcol, jlast + 1));
         k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, y_of<T>(G), G.kcol, G.W);
         CU_LAUNCH(ctx);
-        const T *u = precond(G.W, G.Z);
+        const T *u = precond(G.W, G.Z, nullptr);
         if (!u) return MLPG_ERR_CUDA;
         k_axpy1<T><<<nblk(N), kBlock, 0, s>>>(N, u, x);
         CU_LAUNCH(ctx);
@@ -589,10 +609,10 @@ mlpg_status inner_solve<double>(mlpg_ctx *ctx, const double *b, double *x, doubl
     MLPG_TRY(gmres_alloc(ctx, ctx->g64, ctx->n, ctx->m, ctx->opt.inner_restart));
     CU(ctx, cudaMemsetAsync(x, 0, sizeof(double) * ctx->n * ctx->m, ctx->stream));
     ApplyFn<double> A = [ctx](const double *X, const double *B, double *Y) { return apply_L64_res(ctx, X, B, Y); };
-    PrecFn<double> P = [ctx](const double *v, double *z) { return apply_prec<double>(ctx, v, z); };
+    PrecFn<double> P = [ctx](double *v, double *z, const double *sc) { return apply_prec<double>(ctx, v, z, sc); };
     int64_t its = 0;
     mlpg_status st = gmres_solve<double>(ctx, ctx->g64, A, P, b, x, tol, ctx->opt.max_inner,
-                                         ctx->opt.check_every, &its);
+                                         ctx->opt.check_every, &its, CycleFn(), nullptr, true);
     ctx->st.last_inner_iters += its;
     ctx->st.last_inner_solves += 1;
     return st;
@@ -603,10 +623,10 @@ mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double t
     MLPG_TRY(gmres_alloc(ctx, ctx->g32, ctx->n, ctx->m, ctx->opt.mixed_restart));
     CU(ctx, cudaMemsetAsync(x, 0, sizeof(float) * ctx->n * ctx->m, ctx->stream));
     ApplyFn<float> A = [ctx](const float *X, const float *B, float *Y) { return apply_L32_res(ctx, X, B, Y); };
-    PrecFn<float> P = [ctx](const float *v, float *z) { return apply_prec<float>(ctx, v, z); };
+    PrecFn<float> P = [ctx](float *v, float *z, const double *sc) { return apply_prec<float>(ctx, v, z, sc); };
     int64_t its = 0;
     mlpg_status st = gmres_solve<float>(ctx, ctx->g32, A, P, b, x, tol, ctx->opt.max_inner,
-                                        ctx->opt.check_every, &its);
+                                        ctx->opt.check_every, &its, CycleFn(), nullptr, true);
     ctx->st.last_inner_iters += its;
     ctx->st.last_inner_solves += 1;
     return st;
@@ -707,8 +727,10 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     };
     ctx->cur_inner_tol = inner_tol;
     int64_t oits = 0;
+    const bool phi_zero = Phi_io == nullptr;   // then L^{-1} MS Phi_0 = 0
+    if (phi_zero) CU(ctx, cudaMemsetAsync(xacc, 0, sizeof(T) * N, s));
     MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol, ctx->opt.max_outer, 1,
-                                 &oits, on_cycle, &slot));
+                                 &oits, on_cycle, &slot, phi_zero));
     ctx->st.last_outer_iters += (int32_t)oits;
     // Psi = L^{-1} MS Phi + b_psi
     k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, xacc, bpsi, Psi_out);

@@ -542,19 +542,33 @@ __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const in
 // (kB x kB x m floats, contiguous) is streamed with 16-byte loads.  Thread
 // (a, c) computes z[member_a][4c .. 4c+3] = sum_b Pinv[a][b][4c..] * v[b][4c..].
 // Requires m % 4 == 0 (the caller falls back to k_bjacobi_scalar otherwise).
+// With sc != null the input rows are first scaled by sc[direction] and the
+// scaled rows written back to v (the GMRES basis normalisation, fused here).
 template <typename T>
 __global__ void __launch_bounds__(256) k_bjacobi_blk(int64_t nblk, int m, const int32_t *__restrict__ bmember,
-                                                     const float *__restrict__ Pinv, const T *__restrict__ v,
-                                                     T *__restrict__ z) {
+                                                     const float *__restrict__ Pinv, T *__restrict__ v,
+                                                     const double *__restrict__ sc, T *__restrict__ z) {
     extern __shared__ unsigned char smem_raw[];
-    T *vs = reinterpret_cast<T *>(smem_raw);   // [kB][m]
+    T *vs = reinterpret_cast<T *>(smem_raw);   // [kB][m], then m scale factors
+    T *ssc = vs + kB * m;
     const int64_t blk = blockIdx.x;
     const int mc = m >> 2;                      // float4 chunks per row
     const int32_t *mem = bmember + blk * kB;
+    if (sc)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) ssc[k] = (T)sc[k];
+    __syncthreads();
     for (int q = threadIdx.x; q < kB * m; q += blockDim.x) {
         int b = q / m, k = q - b * m;
         int32_t j = mem[b];
-        vs[q] = j >= 0 ? v[(int64_t)j * m + k] : (T)0;
+        T val = (T)0;
+        if (j >= 0) {
+            val = v[(int64_t)j * m + k];
+            if (sc) {
+                val *= ssc[k];
+                v[(int64_t)j * m + k] = val;
+            }
+        }
+        vs[q] = val;
     }
     __syncthreads();
     const float4 *P4 = reinterpret_cast<const float4 *>(Pinv + blk * (int64_t)kB * kB * m);
@@ -580,8 +594,8 @@ __global__ void __launch_bounds__(256) k_bjacobi_blk(int64_t nblk, int m, const 
 // general m: one thread per (point of the block, direction)
 template <typename T>
 __global__ void __launch_bounds__(256) k_bjacobi_scalar(int64_t nblk, int m, const int32_t *__restrict__ bmember,
-                                                        const float *__restrict__ Pinv, const T *__restrict__ v,
-                                                        T *__restrict__ z) {
+                                                        const float *__restrict__ Pinv, T *__restrict__ v,
+                                                        const double *__restrict__ sc, T *__restrict__ z) {
     extern __shared__ unsigned char smem_raw[];
     T *vs = reinterpret_cast<T *>(smem_raw);
     const int64_t blk = blockIdx.x;
@@ -589,7 +603,15 @@ __global__ void __launch_bounds__(256) k_bjacobi_scalar(int64_t nblk, int m, con
     for (int q = threadIdx.x; q < kB * m; q += blockDim.x) {
         int b = q / m, k = q - b * m;
         int32_t j = mem[b];
-        vs[q] = j >= 0 ? v[(int64_t)j * m + k] : (T)0;
+        T val = (T)0;
+        if (j >= 0) {
+            val = v[(int64_t)j * m + k];
+            if (sc) {
+                val = (T)((double)val * sc[k]);
+                v[(int64_t)j * m + k] = val;
+            }
+        }
+        vs[q] = val;
     }
     __syncthreads();
     const float *P = Pinv + blk * (int64_t)kB * kB * m;
@@ -839,23 +861,24 @@ template mlpg_status apply_MS<double>(mlpg_ctx *, const double *, double *);
 template mlpg_status apply_MS<float>(mlpg_ctx *, const double *, float *);
 
 template <typename T>
-mlpg_status apply_prec(mlpg_ctx *ctx, const T *v, T *z) {
-    const size_t smem = sizeof(T) * kB * ctx->m;
+mlpg_status apply_prec(mlpg_ctx *ctx, T *v, T *z, const double *sc) {
+    const size_t smem = sizeof(T) * (kB + 1) * ctx->m;
     if (smem > 200 * 1024) return set_err(ctx, MLPG_ERR_ARG, "too many directions for the block preconditioner");
     if (smem > 48 * 1024) {
         CU(ctx, cudaFuncSetAttribute(k_bjacobi_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         CU(ctx, cudaFuncSetAttribute(k_bjacobi_scalar<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
     if ((ctx->m & 3) == 0)
-        k_bjacobi_blk<T><<<(unsigned)ctx->nblk, 256, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember, ctx->Pinv, v, z);
+        k_bjacobi_blk<T><<<(unsigned)ctx->nblk, 256, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember, ctx->Pinv, v,
+                                                                           sc, z);
     else
         k_bjacobi_scalar<T><<<(unsigned)ctx->nblk, 256, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember, ctx->Pinv,
-                                                                              v, z);
+                                                                              v, sc, z);
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
-template mlpg_status apply_prec<double>(mlpg_ctx *, const double *, double *);
-template mlpg_status apply_prec<float>(mlpg_ctx *, const float *, float *);
+template mlpg_status apply_prec<double>(mlpg_ctx *, double *, double *, const double *);
+template mlpg_status apply_prec<float>(mlpg_ctx *, float *, float *, const double *);
 
 // Morton order of the points (host, once per point set) cut into blocks of
 // MLPG_BLOCK_PTS consecutive points.
