@@ -162,6 +162,7 @@ struct mlpg_ctx {
     int32_t *bof = nullptr;     // [n] block * kBlockPts + slot of each point
     float *Pinv = nullptr;      // [nblk][kBlockPts][kBlockPts][m] inverse diagonal blocks of L_m
     double cur_inner_tol = 0.0; // tolerance of the inner solves inside the outer operator
+    long long *d_its = nullptr;  // [2] inner / outer Krylov iterations of the current step (device)
     void *bank64 = nullptr, *bank32 = nullptr;  // inner solutions of the outer basis (+ accumulator)
     double *hist[2] = {nullptr, nullptr};       // previous states for the initial guess
     int nhist = 0;                              // how many of them are valid

@@ -361,6 +361,14 @@ __global__ void k_bank_combine(int64_t N, int kmax, const T *__restrict__ bank,
     acc[e] = (T)s;
 }
 
+// total += sum_m its[m]  (one warp)
+__global__ void k_add_its(int M, const int *__restrict__ its, long long *__restrict__ total) {
+    long long s = 0;
+    for (int m = threadIdx.x; m < M; m += 32) s += its[m];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) *total += s;
+}
+
 template <typename T>
 __global__ void k_axpy1(int64_t N, const T *__restrict__ u, T *__restrict__ x) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -530,11 +538,15 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         k_start<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.nrm2, G.bnorm, G.g, G.beta, G.active, G.kcol, G.resid, tol,
                                                 first_zero ? 1 : 0, G.d_active_count);
         CU_LAUNCH(ctx);
-        CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CU(ctx, cudaStreamSynchronize(s));
-        if (*G.h_active == 0) break;
-        if (total >= (int64_t)max_its * M) {
-            *iters = total;
+        if (!first_zero) {
+            // later cycles: stop when every system has converged.  (A first cycle
+            // from x = 0 always iterates; systems with b = 0 are masked.)
+            CU(ctx, cudaMemcpyAsync(G.h_active, G.d_active_count, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CU(ctx, cudaStreamSynchronize(s));
+            if (*G.h_active == 0) break;
+        }
+        if ((int64_t)cycle * R >= max_its) {
+            k_add_its<<<1, 32, 0, s>>>(M, G.its, ctx->d_its);
             return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
         }
         const T *z = precond(G.V, G.Z, G.beta);
@@ -588,12 +600,10 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
         if (!u) return MLPG_ERR_CUDA;
         k_axpy1<T><<<nblk(N), kBlock, 0, s>>>(N, u, x);
         CU_LAUNCH(ctx);
-        std::vector<int> its(M);
-        CU(ctx, cudaMemcpyAsync(its.data(), G.its, sizeof(int) * M, cudaMemcpyDeviceToHost, s));
-        CU(ctx, cudaStreamSynchronize(s));
-        total = 0;
-        for (int v : its) total += v;
     }
+    // iteration counts stay on the device (summed into ctx->d_its, read once per step)
+    k_add_its<<<1, 32, 0, s>>>(M, G.its, ctx->d_its + (M == 1 ? 1 : 0));
+    CU_LAUNCH(ctx);
     *iters = total;
     return MLPG_OK;
 }
@@ -613,7 +623,7 @@ mlpg_status inner_solve<double>(mlpg_ctx *ctx, const double *b, double *x, doubl
     int64_t its = 0;
     mlpg_status st = gmres_solve<double>(ctx, ctx->g64, A, P, b, x, tol, ctx->opt.max_inner,
                                          ctx->opt.check_every, &its, CycleFn(), nullptr, true);
-    ctx->st.last_inner_iters += its;
+    (void)its;
     ctx->st.last_inner_solves += 1;
     return st;
 }
@@ -627,7 +637,7 @@ mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double t
     int64_t its = 0;
     mlpg_status st = gmres_solve<float>(ctx, ctx->g32, A, P, b, x, tol, ctx->opt.max_inner,
                                         ctx->opt.check_every, &its, CycleFn(), nullptr, true);
-    ctx->st.last_inner_iters += its;
+    (void)its;
     ctx->st.last_inner_solves += 1;
     return st;
 }
@@ -731,7 +741,7 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     if (phi_zero) CU(ctx, cudaMemsetAsync(xacc, 0, sizeof(T) * N, s));
     MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol, ctx->opt.max_outer, 1,
                                  &oits, on_cycle, &slot, phi_zero));
-    ctx->st.last_outer_iters += (int32_t)oits;
+    (void)oits;
     // Psi = L^{-1} MS Phi + b_psi
     k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, xacc, bpsi, Psi_out);
     CU_LAUNCH(ctx);
@@ -759,11 +769,14 @@ static mlpg_status ensure_history(mlpg_ctx *ctx) {
     return MLPG_OK;
 }
 
-static void reset_step_stats(mlpg_ctx *ctx) {
+static mlpg_status reset_step_stats(mlpg_ctx *ctx) {
     ctx->st.last_outer_iters = 0;
     ctx->st.last_inner_iters = 0;
     ctx->st.last_inner_solves = 0;
     ctx->st.last_refinements = 0;
+    if (!ctx->d_its) MLPG_TRY(dalloc(ctx, &ctx->d_its, 2));
+    CU(ctx, cudaMemsetAsync(ctx->d_its, 0, 2 * sizeof(long long), ctx->stream));
+    return MLPG_OK;
 }
 
 static mlpg_status prepare_step(mlpg_ctx *ctx, double dt) {
@@ -772,11 +785,18 @@ static mlpg_status prepare_step(mlpg_ctx *ctx, double dt) {
     for (int f = 0; f < 6; ++f) same_inflow &= ctx->ops_psib[f] == ctx->psi_b[f];
     if (kappa != ctx->kappa || !same_inflow) MLPG_TRY(form_operators(ctx, kappa));
     MLPG_TRY(ensure_step_buffers(ctx));
-    reset_step_stats(ctx);
+    MLPG_TRY(reset_step_stats(ctx));
     return MLPG_OK;
 }
 
 static void finish_step_stats(mlpg_ctx *ctx) {
+    long long its[2] = {0, 0};
+    if (cudaMemcpyAsync(its, ctx->d_its, sizeof(its), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
+        cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
+        ctx->st.last_inner_iters = its[0];
+        ctx->st.last_outer_iters = (int32_t)its[1];
+    }
+    cudaGetLastError();
     ctx->st.steps += 1;
     ctx->st.total_outer_iters += ctx->st.last_outer_iters;
     ctx->st.total_inner_iters += ctx->st.last_inner_iters;
