@@ -122,6 +122,86 @@ __device__ bool rk_point(double px, double py, double s, int S, const double *fx
     return true;
 }
 
+// RK functions at (px, py) for the assembly kernel, writing into the shared
+// table (U, Ux, Uy at [a * stride]).  The first pass stores W and its
+// gradient in the table slots so that the second pass does not repeat the
+// square roots; support tests compare squared distances.  Returns the
+// support mask (bit a set when function a is supported), or 0 when the
+// moment matrix is not positive definite.
+__device__ uint64_t rk_point_tab(double px, double py, double s, int S, const double *fx, const double *fy,
+                                 const double *fR2, const double *finvh, const double *fV, double *U, double *Ux,
+                                 double *Uy, int stride) {
+    double M[3][3] = {{0}}, Dx[3][3] = {{0}}, Dy[3][3] = {{0}};
+    const double is = 1.0 / s;
+    uint64_t mask = 0;
+    for (int a = 0; a < S; ++a) {
+        const double dx = px - fx[a], dy = py - fy[a];
+        const double r2 = dx * dx + dy * dy;
+        if (!(r2 < fR2[a])) {
+            U[a * stride] = 0.0;
+            Ux[a * stride] = 0.0;
+            Uy[a * stride] = 0.0;
+            continue;
+        }
+        mask |= uint64_t(1) << a;
+        const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;
+        const double chi = r2 * ir * finvh[a];
+        const double W = spline_w(chi);
+        const double g = spline_dw(chi) * finvh[a] * ir;
+        const double Wx = g * dx, Wy = g * dy, v = fV[a];
+        U[a * stride] = W;
+        Ux[a * stride] = Wx;
+        Uy[a * stride] = Wy;
+        const double P[3] = {1.0, dx * is, dy * is};
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double pp = P[i] * P[j];
+                M[i][j] += v * W * pp;
+                double ex = ((i == 1) * P[j] + (j == 1) * P[i]) * is;
+                double ey = ((i == 2) * P[j] + (j == 2) * P[i]) * is;
+                Dx[i][j] += v * (ex * W + pp * Wx);
+                Dy[i][j] += v * (ey * W + pp * Wy);
+            }
+    }
+    double L00 = M[0][0];
+    if (!(L00 > 0.0)) return 0;
+    L00 = sqrt(L00);
+    double L10 = M[1][0] / L00, L20 = M[2][0] / L00;
+    double d1 = M[1][1] - L10 * L10;
+    if (!(d1 > 1e-14 * M[1][1])) return 0;
+    double L11 = sqrt(d1);
+    double L21 = (M[2][1] - L20 * L10) / L11;
+    double d2 = M[2][2] - L20 * L20 - L21 * L21;
+    if (!(d2 > 1e-14 * M[2][2])) return 0;
+    double L22 = sqrt(d2);
+    auto solve = [&](double b0, double b1, double b2, double *o) {
+        double y0 = b0 / L00, y1 = (b1 - L10 * y0) / L11, y2 = (b2 - L20 * y0 - L21 * y1) / L22;
+        o[2] = y2 / L22;
+        o[1] = (y1 - L21 * o[2]) / L11;
+        o[0] = (y0 - L10 * o[1] - L20 * o[2]) / L00;
+    };
+    double C[3], Cx[3], Cy[3];
+    solve(1.0, 0.0, 0.0, C);
+    solve(-(Dx[0][0] * C[0] + Dx[0][1] * C[1] + Dx[0][2] * C[2]),
+          -(Dx[1][0] * C[0] + Dx[1][1] * C[1] + Dx[1][2] * C[2]),
+          -(Dx[2][0] * C[0] + Dx[2][1] * C[1] + Dx[2][2] * C[2]), Cx);
+    solve(-(Dy[0][0] * C[0] + Dy[0][1] * C[1] + Dy[0][2] * C[2]),
+          -(Dy[1][0] * C[0] + Dy[1][1] * C[1] + Dy[1][2] * C[2]),
+          -(Dy[2][0] * C[0] + Dy[2][1] * C[1] + Dy[2][2] * C[2]), Cy);
+    for (uint64_t bits = mask; bits; bits &= bits - 1) {
+        const int a = __ffsll((long long)bits) - 1;
+        const double W = U[a * stride], Wx = Ux[a * stride], Wy = Uy[a * stride];
+        const double P1 = (px - fx[a]) * is, P2 = (py - fy[a]) * is;
+        const double PC = C[0] + P1 * C[1] + P2 * C[2];
+        U[a * stride] = W * PC;
+        Ux[a * stride] = W * (C[1] * is + Cx[0] + P1 * Cx[1] + P2 * Cx[2]) + PC * Wx;
+        Uy[a * stride] = W * (C[2] * is + Cy[0] + P1 * Cy[1] + P2 * Cy[2]) + PC * Wy;
+    }
+    return mask;
+}
+
 __device__ int find_col(const int32_t *__restrict__ col, int32_t lo, int32_t hi, int32_t key) {
     hi -= 1;
     while (lo <= hi) {
@@ -146,7 +226,8 @@ struct AsmArgs {
 // mats layout: 0 M0, 1 Mt, 2 Ms, 3-4 G, 5-6 Gt, 7-8 Gs, 9-12 K (xx, xy, yx, yy), 13-16 S_f
 __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
     const int64_t i = blockIdx.x;
-    __shared__ double fx[kMaxS], fy[kMaxS], fR[kMaxS], fV[kMaxS];
+    __shared__ double fx[kMaxS], fy[kMaxS], fR[kMaxS], fV[kMaxS], fR2[kMaxS], finvh[kMaxS];
+    __shared__ uint64_t tMask[kChunk];
     __shared__ int32_t fidx[kMaxS];
     __shared__ int S;
     __shared__ int face_slot[2];
@@ -186,6 +267,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
                     fx[s] = A.x[2 * j];
                     fy[s] = A.x[2 * j + 1];
                     fR[s] = A.R[j];
+                    fR2[s] = A.R[j] * A.R[j];
+                    finvh[s] = 2.0 / A.R[j];
                     fV[s] = A.V[j];
                 }
                 ++s;
@@ -245,8 +328,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
                 int f = -A.labels[c0 + e] - 1;
                 fslot = (f == face_slot[0]) ? 0 : 1;
             }
-            bool ok = rk_point(px, py, scale, nS, fx, fy, fR, fV, tU + tid, tUx + tid, tUy + tid, kChunk);
-            if (!ok) atomicOr(A.flag, 1);
+            uint64_t mk = rk_point_tab(px, py, scale, nS, fx, fy, fR2, finvh, fV, tU + tid, tUx + tid, tUy + tid,
+                                       kChunk);
+            if (!mk) atomicOr(A.flag, 1);
+            tMask[tid] = mk;
             tW[tid] = wq;
             tF[tid] = fslot;
         }
@@ -254,14 +339,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
         for (int qk = 0; qk < cnt; ++qk) {
             const double wq = tW[qk];
             const int fs = tF[qk];
+            const uint64_t mk = tMask[qk];
 #pragma unroll
             for (int k = 0; k < kPPT; ++k) {
                 int p = tid + k * kThreads;
                 if (p >= nS * nS) break;
                 int a = p / nS, b = p - (p / nS) * nS;
+                if (!((mk >> a) & (mk >> b) & 1)) continue;   // both functions must be supported here
                 double ua = tU[a * kChunk + qk];
                 double uax = tUx[a * kChunk + qk], uay = tUy[a * kChunk + qk];
-                if (ua == 0.0 && uax == 0.0 && uay == 0.0) continue;
                 double ub = tU[b * kChunk + qk];
                 double ubx = tUx[b * kChunk + qk], uby = tUy[b * kChunk + qk];
                 if (fs < 0) {
