@@ -61,6 +61,9 @@ typedef struct {
     double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-2 */
     int check_every;       /* inner GMRES: host convergence check interval (steps); default 4 */
     int mixed_restart;     /* MLPG_MIXED: restart length of the FP32 inner GMRES (<= 32); default 10 */
+    int mixed_reorth;      /* MLPG_MIXED: Gram-Schmidt passes in the FP32 inner GMRES: 1 = classical
+                              Gram-Schmidt with one re-orthogonalisation (CGS2), 0 = a single
+                              classical pass; the FP64 solves always use CGS2; default 0 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
 } mlpg_options;
 

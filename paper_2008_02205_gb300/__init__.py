@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int),
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("mixed_inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
-                ("mixed_restart", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("mixed_restart", ctypes.c_int), ("mixed_reorth", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):

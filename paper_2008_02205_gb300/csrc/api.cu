@@ -65,7 +65,8 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
     if (opt->dim != 2 || n < 4 || m < 1 || m > MLPG_MAX_DIR) return MLPG_ERR_ARG;
     if (n >= (int64_t(1) << 31)) return MLPG_ERR_ARG;
     if (opt->inner_restart < 1 || opt->inner_restart > MLPG_MAX_RESTART || opt->outer_restart < 1 ||
-        opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART || opt->check_every < 1 || !(opt->c > 0) ||
+        opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART ||
+        (opt->mixed_reorth != 0 && opt->mixed_reorth != 1) || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
     for (int a = 0; a < opt->dim; ++a)
@@ -207,6 +208,7 @@ void mlpg_default_options(mlpg_options *o) {
     o->mixed_inner_tol = 1e-2;
     o->check_every = 4;
     o->mixed_restart = 10;
+    o->mixed_reorth = 0;
     o->stream = nullptr;
 }
 

@@ -78,6 +78,7 @@ struct Gmres {
     int64_t partial_cap = 0;
     int *h_active = nullptr;   // pinned host mirror: number of active directions
     int *d_active_count = nullptr;
+    bool reorth = true;        // CGS2 (true) or a single classical Gram-Schmidt pass
 };
 
 }  // namespace mlpg

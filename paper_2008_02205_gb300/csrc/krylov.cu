@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(kBlock) k_cgs(int64_t n, int M, int MB, int RB
                                                 double *__restrict__ partial) {
     using A = typename Arith<T>::type;
     constexpr int NACC = MODE == 2 ? 1 : MAXL;
-    __shared__ double sh[kBlock];
+    constexpr int GRP = NACC < 8 ? NACC : 8;     // block sums staged per barrier pair
+    __shared__ double sh[GRP][kBlock];
     const int t = threadIdx.x, ml = t % MB, r = t / MB;
     const int m = blockIdx.y * MB + ml, G = gridDim.x;
     const bool act = r < RB && m < M;
@@ -201,16 +202,32 @@ __global__ void __launch_bounds__(kBlock) k_cgs(int64_t n, int M, int MB, int RB
             }
         }
     }
-    const int nout = MODE == 2 ? 1 : nl;
+    if constexpr (NACC == 1) {   // one output (the norm pass)
+        sh[0][t] = act ? (double)acc[0] : 0.0;
+        __syncthreads();
+        if (r == 0 && m < M) {
+            double s = 0.0;
+            for (int k = 0; k < RB; ++k) s += sh[0][k * MB + ml];
+            partial[(int64_t)m * G + blockIdx.x] = s;
+        }
+        return;
+    }
+    // block sums of GRP outputs at a time: stage, one barrier, all threads reduce over RB
+    const int nout = nl;
 #pragma unroll
-    for (int l = 0; l < NACC; ++l) {
-        if (l < nout) {
-            sh[t] = act ? (double)acc[l] : 0.0;
+    for (int l0 = 0; l0 < NACC; l0 += GRP) {
+        if (l0 < nout) {
+#pragma unroll
+            for (int g = 0; g < GRP; ++g) sh[g][t] = act ? (double)acc[l0 + g] : 0.0;
             __syncthreads();
-            if (r == 0 && m < M) {
-                double s = 0.0;
-                for (int k = 0; k < RB; ++k) s += sh[k * MB + ml];
-                partial[((int64_t)l * M + m) * G + blockIdx.x] = s;
+            const int ng = min(GRP, nout - l0);
+            for (int q = t; q < ng * MB; q += kBlock) {
+                const int g = q / MB, mq = q - g * MB, mm = blockIdx.y * MB + mq;
+                if (mm < M) {
+                    double s = 0.0;
+                    for (int k = 0; k < RB; ++k) s += sh[g][k * MB + mq];
+                    partial[((int64_t)(l0 + g) * M + mm) * G + blockIdx.x] = s;
+                }
             }
             __syncthreads();
         }
@@ -264,7 +281,7 @@ __global__ void k_givens(int M, int R, int j, int G, const double *__restrict__ 
     if (lane != 0) return;
     double hn = sqrt(nrm2);
     double *Hm = H + (int64_t)m * (R + 1) * R;  // Hm[row * R + col]
-    for (int l = 0; l <= j; ++l) Hm[l * R + j] = h1[l * M + m] + h2[l * M + m];
+    for (int l = 0; l <= j; ++l) Hm[l * R + j] = h1[l * M + m] + (h2 ? h2[l * M + m] : 0.0);
     Hm[(j + 1) * R + j] = hn;
     for (int l = 0; l < j; ++l) {
         double c = cs[m * R + l], sv = sn[m * R + l];
@@ -558,7 +575,7 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
             MLPG_TRY(A(z, nullptr, w));
             int gnorm = 0;
             {
-                // CGS2 in three fused passes over V_0..V_j
+                // CGS2 in three fused passes over V_0..V_j (CGS1: two passes, h2 unused)
                 // fewer, longer-running blocks as the basis grows (bounded partial sums)
                 const int nl = j + 1, g1 = grid_rows(n, mp, (nl + 3) / 4);
                 const dim3 grid(g1, mp.mchunks);
@@ -569,16 +586,18 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
                 CU_LAUNCH(ctx);
                 k_reduce<<<rblk, kBlock, 0, s>>>(M, nl, g1, G.partial, G.h);
                 CU_LAUNCH(ctx);
-                launch_cgs<T, 1>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.h, w, G.partial);
-                CU_LAUNCH(ctx);
-                k_reduce<<<rblk, kBlock, 0, s>>>(M, nl, g1, G.partial, G.h2);
-                CU_LAUNCH(ctx);
-                launch_cgs<T, 2>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.h2, w, G.partial);
+                if (G.reorth) {
+                    launch_cgs<T, 1>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.h, w, G.partial);
+                    CU_LAUNCH(ctx);
+                    k_reduce<<<rblk, kBlock, 0, s>>>(M, nl, g1, G.partial, G.h2);
+                    CU_LAUNCH(ctx);
+                }
+                launch_cgs<T, 2>(grid, s, n, M, mp.MB, mp.RB, nl, G.V, vs, G.reorth ? G.h2 : G.h, w, G.partial);
                 CU_LAUNCH(ctx);
                 gnorm = g1;   // the norm partials are reduced inside k_givens
             }
             CU(ctx, cudaMemsetAsync(G.d_active_count, 0, sizeof(int), s));
-            k_givens<<<wblk, kBlock, 0, s>>>(M, R, j, gnorm, G.partial, G.h, G.h2, G.H, G.cs, G.sn, G.g, G.beta,
+            k_givens<<<wblk, kBlock, 0, s>>>(M, R, j, gnorm, G.partial, G.h, G.reorth ? G.h2 : nullptr, G.H, G.cs, G.sn, G.g, G.beta,
                                              G.active, G.kcol, G.its, G.resid, G.bnorm, tol, G.d_active_count);
             CU_LAUNCH(ctx);
             jlast = j;
@@ -631,6 +650,7 @@ mlpg_status inner_solve<double>(mlpg_ctx *ctx, const double *b, double *x, doubl
 template <>
 mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double tol) {
     MLPG_TRY(gmres_alloc(ctx, ctx->g32, ctx->n, ctx->m, ctx->opt.mixed_restart));
+    ctx->g32.reorth = ctx->opt.mixed_reorth != 0;
     CU(ctx, cudaMemsetAsync(x, 0, sizeof(float) * ctx->n * ctx->m, ctx->stream));
     ApplyFn<float> A = [ctx](const float *X, const float *B, float *Y) { return apply_L32_res(ctx, X, B, Y); };
     PrecFn<float> P = [ctx](float *v, float *z, const double *sc) { return apply_prec<float>(ctx, v, z, sc); };

@@ -55,3 +55,36 @@ def test_product_never_imports_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h")):
                 txt = open(os.path.join(dp, f)).read()
                 assert "oracle" not in txt.lower() or f.endswith(".py") and "import oracle" not in txt, f
+
+
+def _c_layout(tmp_path, struct, fields):
+    """Offsets and size of a header struct, as gcc lays it out on this machine."""
+    src = tmp_path / f"{struct}.c"
+    body = "".join(f'    printf("{f} %zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "mlpg.h"\nint main(void) {\n'
+                   f'{body}    printf("__size__ %zu\\n", sizeof({struct}));\n    return 0;\n}}\n')
+    exe = tmp_path / struct
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {k: int(v) for k, v in (line.split() for line in out.splitlines())}
+
+
+@pytest.mark.parametrize("struct,cls", [("mlpg_options", "Options"), ("mlpg_stats", "Stats")])
+def test_binding_structs_match_header_layout(tmp_path, struct, cls):
+    import paper_2008_02205_gb300 as pkg
+    C = getattr(pkg, cls)
+    names = [f for f, _ in C._fields_]
+    want = _c_layout(tmp_path, struct, names)
+    for f in names:
+        assert getattr(C, f).offset == want[f], (struct, f)
+    assert ctypes.sizeof(C) == want["__size__"]
+
+
+def test_default_options(lib):
+    import paper_2008_02205_gb300 as pkg
+    o = pkg.mlpg_default_options()
+    assert (o.precision, o.inner_restart, o.mixed_restart, o.check_every) == (0, 20, 10, 4)
+    assert o.mixed_reorth == 0
+    assert (o.inner_tol, o.outer_tol, o.mixed_inner_tol) == (1e-12, 1e-12, 1e-2)

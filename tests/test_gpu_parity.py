@@ -115,10 +115,14 @@ def test_config_1024_points_S4_10_steps_fp64():
     assert _rel(phi, ref) < 1e-9
 
 
-def test_config_1024_points_mixed():
+@pytest.mark.parametrize("reorth", [0, 1])
+def test_config_1024_points_mixed(reorth):
+    """Mixed precision with single-pass or CGS2 Gram-Schmidt in the FP32
+    correction solves: the FP64 refinement brings both to the oracle's flux."""
     prob = mi.small_2d(32, sn=4, seed=1000, steps=10, dt=0.01)
     ref, *_ = _oracle_run(prob)
-    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, refine_tol=1e-12) as tp:
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, refine_tol=1e-12,
+                                           mixed_reorth=reorth) as tp:
         tp.integrate().assemble()
         phi = tp.run(prob.dt, prob.steps)
         st = tp.stats()
