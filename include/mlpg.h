@@ -60,10 +60,16 @@ typedef struct {
     int max_refine;        /* MLPG_MIXED: refinement sweeps per step; default 12 */
     double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-2 */
     int check_every;       /* inner GMRES: host convergence check interval (steps); default 4 */
-    int mixed_restart;     /* MLPG_MIXED: restart length of the FP32 inner GMRES (<= 32); default 10 */
+    int mixed_restart;     /* MLPG_MIXED: restart length of the FP32 inner GMRES (<= 32); default 20.
+                              The FP32 correction solves keep the iterate reached at their iteration
+                              caps (max_inner; one outer restart cycle): the FP64 step residual alone
+                              decides convergence (MLPG_ERR_NOT_CONVERGED after max_refine sweeps) */
     int mixed_reorth;      /* MLPG_MIXED: Gram-Schmidt passes in the FP32 inner GMRES: 1 = classical
                               Gram-Schmidt with one re-orthogonalisation (CGS2), 0 = a single
                               classical pass; the FP64 solves always use CGS2; default 0 */
+    int mixed_half_prec;   /* MLPG_MIXED: 1 = the FP32 correction solves use the block-Jacobi
+                              inverses stored in FP16 (scaled by a power of two per block and
+                              direction), 0 = FP32 inverses; default 1 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
 } mlpg_options;
 
@@ -132,6 +138,18 @@ mlpg_status mlpg_assemble(mlpg_ctx *ctx);
  * angular recovery.  dt = INFINITY solves the steady problem.  Changing dt
  * only re-forms the operators.  MLPG_ERR_NOT_CONVERGED on an iteration cap. */
 mlpg_status mlpg_step(mlpg_ctx *ctx, double dt);
+
+/* One backward-Euler step (as mlpg_step) of each of `count` independent
+ * problems, run concurrently: the caller's thread steps ctxs[0] and one host
+ * thread per further context steps the others, each on its own context
+ * stream, so their kernels overlap on the device.  dt[i] is problem i's step.
+ * The contexts must be distinct and must not share a stream (contexts created
+ * with a NULL stream own one): otherwise MLPG_ERR_ARG before any step.
+ * Returns MLPG_OK when every step succeeded, else the first failing status in
+ * index order; each context's mlpg_last_error describes its own failure.  The
+ * paper states the problem for one point set; batching independent problems
+ * has no counterpart there. */
+mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count);
 
 /* Scalar flux: kind 0 = point values phi_i = sum_j V_j U_j(x_i) Phi_j
  * (Eq. flux-expansion), kind 1 = coefficients Phi_i.  out[n], host. */

@@ -266,3 +266,24 @@ def lognormal_3d(n_per_dim: int = 40, sn: int = 8, seed: int = 3000, steps: int 
         return 0.8 * sig_t
     return make_problem(f"3d-lognormal-{n_per_dim}^3-S{sn}", n_per_dim, 3, sn, seed,
                         st, ss, 0.0, dt, steps, inflow={0: 1.0})
+
+
+def batched_2d(count: int = 64, seed: int = 4000, n_range=(1024, 65536),
+               sn_choices=(4, 6, 8, 10, 12), steps: int = 10, dt: float = 0.01):
+    """Independent 2D problems for batched runs: per problem the point count is
+    log-uniform in n_range (rounded to a k x k lattice), S_N is drawn from
+    sn_choices, sigma_t is uniform in [0.1, 10] and the scattering ratio
+    uniform in [0, 0.99] (both constant over the problem), q = 1, vacuum
+    boundaries.  Problem b uses lattice seed seed + b; the draws come from
+    numpy PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for b in range(count):
+        npts = np.exp(rng.uniform(np.log(n_range[0]), np.log(n_range[1])))
+        k = max(2, int(round(np.sqrt(npts))))
+        sn = int(rng.choice(np.asarray(sn_choices)))
+        sig_t = float(rng.uniform(0.1, 10.0))
+        ratio = float(rng.uniform(0.0, 0.99))
+        out.append(make_problem(f"2d-batch{b}-{k}x{k}-S{sn}", k, 2, sn, seed + b,
+                                sig_t, ratio * sig_t, 1.0, dt, steps))
+    return out

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("mixed_inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("mixed_restart", ctypes.c_int), ("mixed_reorth", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("mixed_half_prec", ctypes.c_int), ("stream", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -82,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "mlpg_integrate": (i32, [_P]),
         "mlpg_assemble": (i32, [_P]),
         "mlpg_step": (i32, [_P, dbl]),
+        "mlpg_step_batch": (i32, [_P, _P, ctypes.c_int]),
         "mlpg_scalar_flux": (i32, [_P, _P, ctypes.c_int]),
         "mlpg_scalar_flux_dev": (i32, [_P, _P, ctypes.c_int]),
         "mlpg_get_state": (i32, [_P, _P]),
@@ -179,6 +180,17 @@ def mlpg_assemble(ctx):
 
 def mlpg_step(ctx, dt):
     _check(ctx, load_library().mlpg_step(ctx, dt))
+
+
+def mlpg_step_batch(ctxs, dts):
+    """One step of each context, run concurrently (distinct contexts and streams)."""
+    k = len(ctxs)
+    arr = (_P * max(k, 1))(*ctxs)
+    d = _arr(np.broadcast_to(np.asarray(dts, dtype=np.float64), (k,)))
+    st = load_library().mlpg_step_batch(arr, _ptr(d), k)
+    if st != MLPG_OK:
+        msgs = [(load_library().mlpg_last_error(c) or b"").decode() for c in ctxs]
+        raise MlpgError(st, "; ".join(f"[{i}] {m}" for i, m in enumerate(msgs) if m))
 
 
 def mlpg_scalar_flux(ctx, n, kind=0):
@@ -296,6 +308,11 @@ class TransportProblem:
         for _ in range(steps):
             mlpg_step(self.ctx, dt)
         return self.scalar_flux()
+
+    @staticmethod
+    def step_batch(problems, dt):
+        """One step of each TransportProblem, concurrently on their own streams."""
+        mlpg_step_batch([p.ctx for p in problems], dt)
 
     def scalar_flux(self, kind=0):
         return mlpg_scalar_flux(self.ctx, self.n, kind)

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "internal.h"
 
@@ -66,7 +67,8 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
     if (n >= (int64_t(1) << 31)) return MLPG_ERR_ARG;
     if (opt->inner_restart < 1 || opt->inner_restart > MLPG_MAX_RESTART || opt->outer_restart < 1 ||
         opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART ||
-        (opt->mixed_reorth != 0 && opt->mixed_reorth != 1) || opt->check_every < 1 || !(opt->c > 0) ||
+        (opt->mixed_reorth != 0 && opt->mixed_reorth != 1) ||
+        (opt->mixed_half_prec != 0 && opt->mixed_half_prec != 1) || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
     for (int a = 0; a < opt->dim; ++a)
@@ -207,8 +209,9 @@ void mlpg_default_options(mlpg_options *o) {
     o->max_refine = 12;
     o->mixed_inner_tol = 1e-2;
     o->check_every = 4;
-    o->mixed_restart = 10;
+    o->mixed_restart = 20;
     o->mixed_reorth = 0;
+    o->mixed_half_prec = 1;
     o->stream = nullptr;
 }
 
@@ -306,6 +309,31 @@ mlpg_status mlpg_step(mlpg_ctx *ctx, double dt) {
         return ctx->opt.precision == MLPG_MIXED ? step_mixed(ctx, dt) : step_fp64(ctx, dt);
     }
     CATCH_ALL(ctx)
+}
+
+mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count) {
+    if (!ctxs || !dt || count < 0) return MLPG_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) return MLPG_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i] || ctxs[j]->stream == ctxs[i]->stream)
+                return set_err(ctxs[i], MLPG_ERR_ARG, "batched contexts must be distinct and on distinct streams");
+    }
+    if (count == 0) return MLPG_OK;
+    std::vector<mlpg_status> st(count, MLPG_OK);
+    std::vector<std::thread> th;
+    int next = 1;   // contexts [next, count) still to run on the caller's thread
+    try {
+        th.reserve(count - 1);
+        for (; next < count; ++next) th.emplace_back([&st, ctxs, dt, i = next] { st[i] = mlpg_step(ctxs[i], dt[i]); });
+    } catch (...) {   // no thread: run the rest here
+    }
+    st[0] = mlpg_step(ctxs[0], dt[0]);
+    for (int i = next; i < count; ++i) st[i] = mlpg_step(ctxs[i], dt[i]);
+    for (auto &t : th) t.join();
+    for (int i = 0; i < count; ++i)
+        if (st[i] != MLPG_OK) return st[i];
+    return MLPG_OK;
 }
 
 mlpg_status mlpg_scalar_flux_dev(mlpg_ctx *ctx, double *out, int kind) {

@@ -162,6 +162,8 @@ struct mlpg_ctx {
     int32_t *bmember = nullptr; // [nblk * kBlockPts] point of each block slot (-1: empty)
     int32_t *bof = nullptr;     // [n] block * kBlockPts + slot of each point
     float *Pinv = nullptr;      // [nblk][kBlockPts][kBlockPts][m] inverse diagonal blocks of L_m
+    uint16_t *Pinv16 = nullptr; // same, FP16 bits scaled by Pscale^-1 (mixed mode), or null
+    float *Pscale = nullptr;    // [nblk][m] power-of-two decode factor of each FP16 block
     double cur_inner_tol = 0.0; // tolerance of the inner solves inside the outer operator
     long long *d_its = nullptr;  // [2] inner / outer Krylov iterations of the current step (device)
     void *bank64 = nullptr, *bank32 = nullptr;  // inner solutions of the outer basis (+ accumulator)

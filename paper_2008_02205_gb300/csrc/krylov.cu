@@ -506,11 +506,13 @@ using CycleFn = std::function<mlpg_status(const double *y, const float *y32, con
 
 // Solve A x = b for all M systems, right preconditioned by P (identity when
 // empty); x holds the initial guess.  Returns the summed iteration count in
-// *iters and MLPG_ERR_NOT_CONVERGED on the cap.
+// *iters and MLPG_ERR_NOT_CONVERGED on the cap; with cap_ok the iterate
+// reached at the cap is kept instead (an approximate solve).
 template <typename T>
 static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, const PrecFn<T> &P, const T *b,
                                T *x, double tol, int max_its, int check_every, int64_t *iters,
-                               const CycleFn &on_cycle = CycleFn(), int *slot = nullptr, bool x_zero = false) {
+                               const CycleFn &on_cycle = CycleFn(), int *slot = nullptr, bool x_zero = false,
+                               bool cap_ok = false) {
     const int64_t n = G.n, N = n * G.M;
     const int M = G.M, R = G.R;
     const int64_t vs = N;
@@ -536,6 +538,8 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
     };
     int64_t total = 0;
     for (int cycle = 0;; ++cycle) {
+        // an approximate solve (cap_ok) keeps its iterate at the cap, without a final residual
+        if (cap_ok && cycle > 0 && (int64_t)cycle * R >= max_its) break;
         const bool first_zero = cycle == 0 && x_zero;   // r = b: no operator apply needed
         if (cycle == 0 && !x_zero) {
             MLPG_TRY(norm2(b));
@@ -656,7 +660,7 @@ mlpg_status inner_solve<float>(mlpg_ctx *ctx, const float *b, float *x, double t
     PrecFn<float> P = [ctx](float *v, float *z, const double *sc) { return apply_prec<float>(ctx, v, z, sc); };
     int64_t its = 0;
     mlpg_status st = gmres_solve<float>(ctx, ctx->g32, A, P, b, x, tol, ctx->opt.max_inner,
-                                        ctx->opt.check_every, &its, CycleFn(), nullptr, true);
+                                        ctx->opt.check_every, &its, CycleFn(), nullptr, true, true);
     (void)its;
     ctx->st.last_inner_solves += 1;
     return st;
@@ -759,8 +763,14 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     int64_t oits = 0;
     const bool phi_zero = Phi_io == nullptr;   // then L^{-1} MS Phi_0 = 0
     if (phi_zero) CU(ctx, cudaMemsetAsync(xacc, 0, sizeof(T) * N, s));
-    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol, ctx->opt.max_outer, 1,
-                                 &oits, on_cycle, &slot, phi_zero));
+    // In a mixed-precision correction (T = float) the outer solve is one
+    // restart cycle at most and its iterate is kept: the FP64 step residual
+    // decides convergence, and the inexact inner solves inside the operator
+    // can hold the outer residual near its own tolerance.
+    const bool correction = sizeof(T) == 4;
+    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol,
+                                 correction ? Rout : ctx->opt.max_outer, 1, &oits, on_cycle, &slot, phi_zero,
+                                 correction));
     (void)oits;
     // Psi = L^{-1} MS Phi + b_psi
     k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, xacc, bpsi, Psi_out);

@@ -19,6 +19,9 @@
 // per boundary row.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
+
+#include <cuda_fp16.h>
 
 #include "internal.h"
 
@@ -287,7 +290,24 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
         acc[t] = 0.0f;
     }
     const int32_t p1 = rowptr[row + 1];
-    for (int32_t p = rowptr[row]; p < p1; ++p) {
+    int32_t p = rowptr[row];
+    for (; p + 1 < p1; p += 2) {   // two entries in flight
+        const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)lane, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)lane;
+        const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
+                    a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
+        const float b0 = A32[p + 1], b1 = A32[nnz + p + 1], b2 = A32[2 * nnz + p + 1], b3 = A32[3 * nnz + p + 1],
+                    b4 = A32[4 * nnz + p + 1], b5 = A32[5 * nnz + p + 1];
+#pragma unroll
+        for (int t = 0; t < DPL; ++t) {
+            if (on[t]) {
+                const float x0 = X[jb0 + t * TM], x1 = X[jb1 + t * TM];
+                float v0 = fmaf(c5[t], a5, fmaf(c4[t], a4, fmaf(c3[t], a3, fmaf(c2[t], a2, fmaf(c1[t], a1, a0)))));
+                float v1 = fmaf(c5[t], b5, fmaf(c4[t], b4, fmaf(c3[t], b3, fmaf(c2[t], b2, fmaf(c1[t], b1, b0)))));
+                acc[t] = fmaf(v1, x1, fmaf(v0, x0, acc[t]));
+            }
+        }
+    }
+    for (; p < p1; ++p) {
         const IDX jb = (IDX)col[p] * (IDX)m + (IDX)lane;
         const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
                     a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
@@ -471,6 +491,7 @@ __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const in
                                                    const double *__restrict__ coef, const double *__restrict__ fcoef,
                                                    const int32_t *__restrict__ bmember,
                                                    const int32_t *__restrict__ bof, float *__restrict__ Pinv,
+                                                   uint16_t *__restrict__ Pinv16, float *__restrict__ Pscale,
                                                    int *__restrict__ flag) {
     __shared__ float sA[8][kB][2 * kB + 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -531,10 +552,23 @@ __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const in
         if (lane == 0) atomicOr(flag, 32);
         return;
     }
+    float amax = 0.0f;
     for (int e = lane; e < kB * kB; e += 32) {
         int a = e / kB, b = e - a * kB;
         Pinv[((k * kB + a) * kB + b) * (int64_t)m + dir] = A[a][kB + b];
+        amax = fmaxf(amax, fabsf(A[a][kB + b]));
     }
+    if (!Pinv16) return;
+    // FP16 copy: amax = f 2^ex with f in [0.5, 1); entries scaled by 2^(14 - ex) stay below 2^14
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    int ex = 0;
+    if (amax > 0.0f) frexpf(amax, &ex);
+    const float enc = amax > 0.0f ? ldexpf(1.0f, 14 - ex) : 1.0f;
+    for (int e = lane; e < kB * kB; e += 32) {
+        int a = e / kB, b = e - a * kB;
+        Pinv16[((k * kB + a) * kB + b) * (int64_t)m + dir] = __half_as_ushort(__float2half_rn(A[a][kB + b] * enc));
+    }
+    if (lane == 0) Pscale[k * (int64_t)m + dir] = amax > 0.0f ? ldexpf(1.0f, ex - 14) : 1.0f;
 }
 
 // z = P^{-1} v, one CTA per block of kB points.  The kB input rows v[member]
@@ -588,6 +622,73 @@ __global__ void __launch_bounds__(256) k_bjacobi_blk(int64_t nblk, int m, const 
         }
         T *zo = z + (int64_t)i * m + 4 * c;
         zo[0] = acc0; zo[1] = acc1; zo[2] = acc2; zo[3] = acc3;
+    }
+}
+
+// As k_bjacobi_blk with the FP16 inverses of the mixed mode: thread (a, c)
+// owns four directions of row a and reads its sixteen 8-byte inverse entries
+// before the block's input rows are staged (they do not depend on v, so their
+// latency overlaps the gather), then multiplies its sums by the block's
+// power-of-two decode factors.  Requires m % 4 == 0; any block size (tasks
+// beyond the block size loop).
+__global__ void __launch_bounds__(256) k_bjacobi_h16(int64_t nblk, int m, const int32_t *__restrict__ bmember,
+                                                     const uint16_t *__restrict__ Pinv16,
+                                                     const float *__restrict__ Pscale, float *__restrict__ v,
+                                                     const double *__restrict__ sc, float *__restrict__ z) {
+    extern __shared__ unsigned char smem_raw[];
+    float *vs = reinterpret_cast<float *>(smem_raw);   // [kB][m], then m scale factors
+    float *ssc = vs + kB * m;
+    const int64_t blk = blockIdx.x;
+    const int mc = m >> 2, ntask = kB * mc;
+    const int32_t *mem = bmember + blk * kB;
+    const uint2 *P2 = reinterpret_cast<const uint2 *>(Pinv16 + blk * (int64_t)kB * kB * m);
+    const float4 *D4 = reinterpret_cast<const float4 *>(Pscale + blk * (int64_t)m);
+    int t = threadIdx.x;
+    uint2 q[kB];
+    if (t < ntask) {
+        const int a = t / mc, c = t - a * mc;
+#pragma unroll
+        for (int b = 0; b < kB; ++b) q[b] = P2[((int64_t)a * kB + b) * mc + c];
+    }
+    if (sc)
+        for (int k = threadIdx.x; k < m; k += blockDim.x) ssc[k] = (float)sc[k];
+    __syncthreads();
+    for (int e = threadIdx.x; e < kB * m; e += blockDim.x) {
+        int b = e / m, k = e - b * m;
+        int32_t j = mem[b];
+        float val = 0.0f;
+        if (j >= 0) {
+            val = v[(int64_t)j * m + k];
+            if (sc) {
+                val *= ssc[k];
+                v[(int64_t)j * m + k] = val;
+            }
+        }
+        vs[e] = val;
+    }
+    __syncthreads();
+    for (bool first = true; t < ntask; t += blockDim.x, first = false) {
+        const int a = t / mc, c = t - a * mc;
+        if (!first) {
+#pragma unroll
+            for (int b = 0; b < kB; ++b) q[b] = P2[((int64_t)a * kB + b) * mc + c];
+        }
+        const int32_t i = mem[a];
+        if (i < 0) continue;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll
+        for (int b = 0; b < kB; ++b) {
+            const float2 p01 = __half22float2(*reinterpret_cast<const __half2 *>(&q[b].x));
+            const float2 p23 = __half22float2(*reinterpret_cast<const __half2 *>(&q[b].y));
+            const float *vb = vs + b * m + 4 * c;
+            acc0 = fmaf(p01.x, vb[0], acc0);
+            acc1 = fmaf(p01.y, vb[1], acc1);
+            acc2 = fmaf(p23.x, vb[2], acc2);
+            acc3 = fmaf(p23.y, vb[3], acc3);
+        }
+        const float4 d = D4[c];
+        float *zo = z + (int64_t)i * m + 4 * c;
+        zo[0] = acc0 * d.x; zo[1] = acc1 * d.y; zo[2] = acc2 * d.z; zo[3] = acc3 * d.w;
     }
 }
 
@@ -680,6 +781,10 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     MLPG_TRY(dalloc(ctx, &ctx->r64, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->abc, 5 * n));   // [3][n] FP64 products + [3][n] float copy
     MLPG_TRY(dalloc(ctx, &ctx->Pinv, (size_t)ctx->nblk * kB * kB * m));
+    if (ctx->opt.precision == MLPG_MIXED && ctx->opt.mixed_half_prec && (m & 3) == 0) {
+        MLPG_TRY(dalloc(ctx, &ctx->Pinv16, (size_t)ctx->nblk * kB * kB * m));
+        MLPG_TRY(dalloc(ctx, &ctx->Pscale, (size_t)ctx->nblk * m));
+    }
     // boundary segment (the face arrays do not depend on dt)
     int *cnt;
     MLPG_TRY(dalloc(ctx, &cnt, n));
@@ -742,7 +847,8 @@ mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
     {
         dim3 grid((unsigned)ctx->nblk, (unsigned)((m + 7) / 8));
         k_block_inv<<<grid, 256, 0, s>>>(ctx->nblk, m, ctx->rowptr, ctx->col, nnz, ctx->A64, Sf, ctx->coef,
-                                         ctx->fcoef, ctx->bmember, ctx->bof, ctx->Pinv, ctx->d_flag);
+                                         ctx->fcoef, ctx->bmember, ctx->bof, ctx->Pinv, ctx->Pinv16, ctx->Pscale,
+                                         ctx->d_flag);
         CU_LAUNCH(ctx);
         CU(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
@@ -867,6 +973,17 @@ mlpg_status apply_prec(mlpg_ctx *ctx, T *v, T *z, const double *sc) {
     if (smem > 48 * 1024) {
         CU(ctx, cudaFuncSetAttribute(k_bjacobi_blk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         CU(ctx, cudaFuncSetAttribute(k_bjacobi_scalar<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CU(ctx, cudaFuncSetAttribute(k_bjacobi_h16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        if (ctx->Pinv16) {   // one thread per (row, four directions) task, up to 256
+            const int ntask = kB * (ctx->m >> 2);
+            const int bs = ntask >= 256 ? 256 : (ntask + 31) / 32 * 32;
+            k_bjacobi_h16<<<(unsigned)ctx->nblk, bs, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember,
+                                                                          ctx->Pinv16, ctx->Pscale, v, sc, z);
+            CU_LAUNCH(ctx);
+            return MLPG_OK;
+        }
     }
     if ((ctx->m & 3) == 0)
         k_bjacobi_blk<T><<<(unsigned)ctx->nblk, 256, smem, ctx->stream>>>(ctx->nblk, ctx->m, ctx->bmember, ctx->Pinv, v,

@@ -44,6 +44,9 @@ def test_null_arguments_rejected_without_device(lib):
     # argument checks happen before any CUDA call
     lib.mlpg_create.restype = ctypes.c_int
     assert lib.mlpg_create(None, 0, None, None, 0, None, None, None, None, None, None) == -1
+    lib.mlpg_step_batch.restype = ctypes.c_int
+    assert lib.mlpg_step_batch(None, None, 1) == -1
+    assert lib.mlpg_step_batch((ctypes.c_void_p * 1)(None), (ctypes.c_double * 1)(0.1), 1) == -1
     lib.mlpg_last_error.restype = ctypes.c_char_p
     assert lib.mlpg_last_error(None) == b"null context"
 
@@ -85,6 +88,6 @@ def test_binding_structs_match_header_layout(tmp_path, struct, cls):
 def test_default_options(lib):
     import paper_2008_02205_gb300 as pkg
     o = pkg.mlpg_default_options()
-    assert (o.precision, o.inner_restart, o.mixed_restart, o.check_every) == (0, 20, 10, 4)
-    assert o.mixed_reorth == 0
+    assert (o.precision, o.inner_restart, o.mixed_restart, o.check_every) == (0, 20, 20, 4)
+    assert (o.mixed_reorth, o.mixed_half_prec) == (0, 1)
     assert (o.inner_tol, o.outer_tol, o.mixed_inner_tol) == (1e-12, 1e-12, 1e-2)

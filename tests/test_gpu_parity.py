@@ -115,19 +115,45 @@ def test_config_1024_points_S4_10_steps_fp64():
     assert _rel(phi, ref) < 1e-9
 
 
-@pytest.mark.parametrize("reorth", [0, 1])
-def test_config_1024_points_mixed(reorth):
-    """Mixed precision with single-pass or CGS2 Gram-Schmidt in the FP32
-    correction solves: the FP64 refinement brings both to the oracle's flux."""
+@pytest.mark.parametrize("reorth,half", [(0, 1), (1, 0), (0, 0)])
+def test_config_1024_points_mixed(reorth, half):
+    """Mixed precision with CGS2 or single-pass Gram-Schmidt, FP32 or FP16
+    block inverses in the FP32 correction solves: the FP64 refinement brings
+    every variant to the oracle's flux."""
     prob = mi.small_2d(32, sn=4, seed=1000, steps=10, dt=0.01)
     ref, *_ = _oracle_run(prob)
     with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, refine_tol=1e-12,
-                                           mixed_reorth=reorth) as tp:
+                                           mixed_reorth=reorth, mixed_half_prec=half) as tp:
         tp.integrate().assemble()
         phi = tp.run(prob.dt, prob.steps)
         st = tp.stats()
     assert _rel(phi, ref) < 1e-8
     assert st["last_refinements"] >= 1
+
+
+@pytest.mark.parametrize("precision,tol", [(pkg.MLPG_FP64, 1e-9), (pkg.MLPG_MIXED, 1e-8)])
+def test_batched_problems_step_concurrently(precision, tol):
+    """Independent problems (log-uniform sizes, S4-S12, sigma_t in [0.1, 10],
+    scattering ratio in [0, 0.99]) stepped together by mlpg_step_batch, one
+    stream each: every scalar flux matches its own oracle run."""
+    probs = mi.batched_2d(4, seed=4100, n_range=(64, 400), steps=3)
+    refs = [_oracle_run(p)[0] for p in probs]
+    tps = [pkg.TransportProblem.from_problem(p, precision=precision, inner_tol=1e-13, outer_tol=1e-13,
+                                             refine_tol=1e-12) for p in probs]
+    try:
+        for tp in tps:
+            tp.integrate().assemble()
+        for _ in range(probs[0].steps):
+            pkg.TransportProblem.step_batch(tps, probs[0].dt)
+        for tp, ref in zip(tps, refs):
+            assert _rel(tp.scalar_flux(), ref) < tol
+        # the same context twice in one batch is refused before any step
+        with pytest.raises(pkg.MlpgError):
+            pkg.mlpg_step_batch([tps[0].ctx, tps[0].ctx], probs[0].dt)
+        assert tps[0].stats()["steps"] == probs[0].steps
+    finally:
+        for tp in tps:
+            tp.close()
 
 
 def test_steady_with_inflow_and_two_region():
