@@ -15,6 +15,8 @@
  *   B. overlap connectivity by brute force                           Sec. 3.4
  *   C. Voronoi-like cells by half-plane clipping of the kernel box   Sec. 3.1
  *   D. quadrature points of the fan triangles and boundary edges     Sec. 3.1-3.2, App. A
+ *   C3/D3. the same in 3D: polyhedral cells, fan tetrahedra, boundary
+ *      triangles                                                    Sec. 3.1-3.2, App. A
  *   E. cubic-spline kernel and linear reproducing-kernel functions   Sec. 2.1-2.2
  *   F. quadrature-outermost integration of the bilinear forms        Sec. 3.2 (Alg. 1), Sec. 4.1
  *
@@ -28,6 +30,8 @@
  *     clipped by the bisector half-planes of every overlap neighbour j != i.
  *   - 2D cells are fanned into triangles (x_i, v_k, v_{k+1}) from the generator,
  *     vertices counter-clockwise; the reference rule is mapped with p0 = x_i.
+ *   - 3D cells are fanned into tetrahedra (x_i, f_0, f_k, f_{k+1}) over a fan
+ *     of every face f; boundary faces into triangles (f_0, f_k, f_{k+1}).
  *   - RK basis P_j(x) = [1, (x - x_j)/s] with s = h of the point owning the
  *     evaluation point (any common scale gives the same U in exact arithmetic).
  */
@@ -149,6 +153,30 @@ int orc_triangle_rule(int n, double *xi, double *w)
 
 /* Gauss-Legendre on [-1, 1] (App. A line map x = p0 + (p1 - p0)(xi + 1)/2). */
 int orc_line_rule(int n, double *t, double *w) { return orc_gauss_jacobi(n, 0.0, 0.0, t, w); }
+
+/* Reference tetrahedron {xi >= 0, xi1 + xi2 + xi3 <= 1}: conical product of
+ * n-point Gauss-Jacobi(2,0) in u, Gauss-Jacobi(1,0) in v and Gauss-Legendre in
+ * s, xi1 = u, xi2 = (1 - u) v, xi3 = (1 - u)(1 - v) s (Jacobian
+ * (1 - u)^2 (1 - v), carried by the Jacobi weights), exact for total degree
+ * 2n - 1.  Point k = (iu*n + iv)*n + is.  xi[3*k], w[k]; sum(w) = 1/6. */
+int orc_tet_rule(int n, double *xi, double *w)
+{
+    double tu[64], wu[64], tv[64], wv[64], ts[64], ws[64];
+    if (orc_gauss_jacobi(n, 2.0, 0.0, tu, wu) || orc_gauss_jacobi(n, 1.0, 0.0, tv, wv) ||
+        orc_gauss_jacobi(n, 0.0, 0.0, ts, ws))
+        return ORC_ERR_ARG;
+    for (int iu = 0; iu < n; ++iu)
+        for (int iv = 0; iv < n; ++iv)
+            for (int is = 0; is < n; ++is) {
+                double u = 0.5 * (tu[iu] + 1.0), v = 0.5 * (tv[iv] + 1.0), r = 0.5 * (ts[is] + 1.0);
+                int k = (iu * n + iv) * n + is;
+                xi[3 * k + 0] = u;
+                xi[3 * k + 1] = (1.0 - u) * v;
+                xi[3 * k + 2] = (1.0 - u) * (1.0 - v) * r;
+                w[k] = (wu[iu] / 8.0) * (wv[iv] / 4.0) * (ws[is] / 2.0);
+            }
+    return ORC_OK;
+}
 
 /* ======================================================================
  * B. Overlap connectivity (Sec. 3.4): j is a neighbour of i when the kernel
@@ -340,6 +368,334 @@ int64_t orc_boundary_qps_2d(int64_t n, const int64_t *cptr, const double *verts,
 }
 
 /* ======================================================================
+ * C3/D3. Cells and quadrature points in 3D (Sec. 3.1-3.2, App. A).
+ * The cell of i is the box [x_i - R_i, x_i + R_i]^3 intersected with the domain,
+ * clipped by the bisector half-space {y : (y - m).(x_j - x_i) <= 0},
+ * m = (x_i + x_j)/2, of every overlap neighbour j != i.  A cell is a list of
+ * planar polygonal faces, each counter-clockwise seen from outside, with the
+ * labels of the 2D cells (domain faces 0:-x 1:+x 2:-y 3:+y 4:-z 5:+z).
+ * Clipping by one half-space: every face polygon is clipped (Sutherland-
+ * Hodgman); the points where face edges cross the plane and the vertices on
+ * it, taken once each, ordered by angle about the plane normal, form the new
+ * face on the plane.  A vertex whose signed distance is within eps of the
+ * plane counts as on it (planes through existing edges, vertices or faces, as
+ * in unjittered lattices); a plane with no vertex beyond eps cuts nothing.
+ * A neighbour whose plane lies beyond the farthest vertex cuts nothing and is
+ * skipped.  The cell is split into tetrahedra (x_i, v_0, v_k, v_k+1) from the
+ * generator over a fan of every face; boundary faces into triangles
+ * (v_0, v_k, v_k+1).
+ * ====================================================================== */
+typedef struct {
+    int nf, cap_f, cap_v;
+    int *nv;       /* [cap_f] vertices of each face */
+    int32_t *lab;  /* [cap_f] label of each face */
+    double *v;     /* [cap_f][cap_v][3] */
+} poly3;
+
+static int poly3_alloc(poly3 *P, int cap_f, int cap_v)
+{
+    P->nf = 0; P->cap_f = cap_f; P->cap_v = cap_v;
+    P->nv = malloc(sizeof(int) * cap_f);
+    P->lab = malloc(sizeof(int32_t) * cap_f);
+    P->v = malloc(sizeof(double) * 3 * (size_t)cap_f * cap_v);
+    return P->nv && P->lab && P->v ? ORC_OK : ORC_ERR_CAP;
+}
+
+static void poly3_free(poly3 *P) { free(P->nv); free(P->lab); free(P->v); }
+
+static double *pv(const poly3 *P, int f, int k) { return P->v + 3 * ((size_t)f * P->cap_v + k); }
+
+static void poly3_box(poly3 *P, const double *b0, const double *b1, const int *on_lo, const int *on_hi)
+{
+    /* corners c[ix + 2 iy + 4 iz]; faces listed counter-clockwise from outside */
+    static const int F[6][4] = {{0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4},
+                                {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
+    double c[8][3];
+    for (int k = 0; k < 8; ++k) {
+        c[k][0] = (k & 1) ? b1[0] : b0[0];
+        c[k][1] = (k & 2) ? b1[1] : b0[1];
+        c[k][2] = (k & 4) ? b1[2] : b0[2];
+    }
+    P->nf = 6;
+    for (int f = 0; f < 6; ++f) {
+        int a = f / 2, hi = f % 2;
+        int dom = hi ? on_hi[a] : on_lo[a];
+        P->lab[f] = dom ? -(f + 1) : LABEL_EXTENT;
+        P->nv[f] = 4;
+        for (int k = 0; k < 4; ++k) memcpy(pv(P, f, k), c[F[f][k]], sizeof(double) * 3);
+    }
+}
+
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+static void cross3(const double *a, const double *b, double *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double poly3_rmax(const poly3 *P, const double *g)
+{
+    double r2 = 0.0;
+    for (int f = 0; f < P->nf; ++f)
+        for (int k = 0; k < P->nv[f]; ++k) {
+            const double *q = pv(P, f, k);
+            double d[3] = {q[0] - g[0], q[1] - g[1], q[2] - g[2]};
+            if (dot3(d, d) > r2) r2 = dot3(d, d);
+        }
+    return sqrt(r2);
+}
+
+/* Clip P by the bisector of (xi, xj) into W, then copy back.  cut[] holds up
+ * to 2 cap_v cap_f points.  tol: length scale of "the same point".  Returns 0,
+ * or ORC_ERR_CAP when a capacity is exceeded. */
+static int poly3_clip(poly3 *P, poly3 *W, double *cut, const double *xi, const double *xj, int32_t j,
+                      double tol)
+{
+    double d[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
+    double m[3] = {0.5 * (xi[0] + xj[0]), 0.5 * (xi[1] + xj[1]), 0.5 * (xi[2] + xj[2])};
+    const double eps = tol * sqrt(dot3(d, d));   /* signed distances s carry a factor |d| */
+    int any_out = 0;
+    for (int f = 0; f < P->nf && !any_out; ++f)
+        for (int k = 0; k < P->nv[f]; ++k) {
+            const double *a = pv(P, f, k);
+            double am[3] = {a[0] - m[0], a[1] - m[1], a[2] - m[2]};
+            if (dot3(am, d) > eps) { any_out = 1; break; }
+        }
+    if (!any_out) return ORC_OK;
+    int nc = 0;
+    W->nf = 0;
+    for (int f = 0; f < P->nf; ++f) {
+        int nv = P->nv[f], out = 0;
+        if (W->nf >= W->cap_f) return ORC_ERR_CAP;
+        for (int k = 0; k < nv; ++k) {
+            const double *a = pv(P, f, k), *b = pv(P, f, (k + 1) % nv);
+            double am[3] = {a[0] - m[0], a[1] - m[1], a[2] - m[2]};
+            double bm[3] = {b[0] - m[0], b[1] - m[1], b[2] - m[2]};
+            double sa = dot3(am, d), sb = dot3(bm, d);
+            if (out + 2 > W->cap_v || nc + 2 > 2 * P->cap_v * P->cap_f) return ORC_ERR_CAP;
+            if (sa <= eps) {                       /* inside or on the plane: kept */
+                memcpy(pv(W, W->nf, out++), a, sizeof(double) * 3);
+                if (sa >= -eps) memcpy(cut + 3 * nc++, a, sizeof(double) * 3);
+            }
+            if ((sa < -eps && sb > eps) || (sa > eps && sb < -eps)) {   /* strict crossing */
+                double t = sa / (sa - sb), *q = pv(W, W->nf, out++);
+                for (int e = 0; e < 3; ++e) q[e] = a[e] + (b[e] - a[e]) * t;
+                memcpy(cut + 3 * nc++, q, sizeof(double) * 3);
+            }
+        }
+        if (out >= 3) {
+            W->nv[W->nf] = out;
+            W->lab[W->nf] = P->lab[f];
+            ++W->nf;
+        }
+    }
+    /* the new face: distinct cut points ordered counter-clockwise about +d */
+    int nu = 0;
+    for (int c = 0; c < nc; ++c) {
+        int dup = 0;
+        for (int u = 0; u < nu && !dup; ++u) {
+            double e[3] = {cut[3 * c] - cut[3 * u], cut[3 * c + 1] - cut[3 * u + 1], cut[3 * c + 2] - cut[3 * u + 2]};
+            dup = sqrt(dot3(e, e)) <= tol;
+        }
+        if (!dup) {
+            memmove(cut + 3 * nu, cut + 3 * c, sizeof(double) * 3);
+            ++nu;
+        }
+    }
+    if (nu >= 3) {
+        if (W->nf >= W->cap_f || nu > W->cap_v) return ORC_ERR_CAP;
+        double dl = sqrt(dot3(d, d)), n[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
+        int a = 0;
+        for (int e = 1; e < 3; ++e)
+            if (fabs(n[e]) < fabs(n[a])) a = e;
+        double e1[3] = {-n[a] * n[0], -n[a] * n[1], -n[a] * n[2]}, e2[3];
+        e1[a] += 1.0;
+        double l1 = sqrt(dot3(e1, e1));
+        for (int e = 0; e < 3; ++e) e1[e] /= l1;
+        cross3(n, e1, e2);
+        double cen[3] = {0, 0, 0};
+        for (int u = 0; u < nu; ++u)
+            for (int e = 0; e < 3; ++e) cen[e] += cut[3 * u + e] / nu;
+        double *ang = malloc(sizeof(double) * nu);
+        int *ord = malloc(sizeof(int) * nu);
+        for (int u = 0; u < nu; ++u) {
+            double r[3] = {cut[3 * u] - cen[0], cut[3 * u + 1] - cen[1], cut[3 * u + 2] - cen[2]};
+            ang[u] = atan2(dot3(r, e2), dot3(r, e1));
+            ord[u] = u;
+        }
+        for (int u = 1; u < nu; ++u) {   /* insertion sort by angle */
+            int o = ord[u], k = u;
+            while (k > 0 && ang[ord[k - 1]] > ang[o]) { ord[k] = ord[k - 1]; --k; }
+            ord[k] = o;
+        }
+        for (int u = 0; u < nu; ++u) memcpy(pv(W, W->nf, u), cut + 3 * ord[u], sizeof(double) * 3);
+        W->nv[W->nf] = nu;
+        W->lab[W->nf] = j;
+        ++W->nf;
+        free(ang); free(ord);
+    }
+    P->nf = W->nf;
+    for (int f = 0; f < W->nf; ++f) {
+        P->nv[f] = W->nv[f];
+        P->lab[f] = W->lab[f];
+        memcpy(pv(P, f, 0), pv(W, f, 0), sizeof(double) * 3 * W->nv[f]);
+    }
+    return ORC_OK;
+}
+
+/* volume of a cell: sum of |det(v0 - g, vk - g, vk+1 - g)| / 6 over the fans */
+static double poly3_volume(const poly3 *P, const double *g)
+{
+    double vol = 0.0;
+    for (int f = 0; f < P->nf; ++f) {
+        const double *v0 = pv(P, f, 0);
+        for (int k = 1; k + 1 < P->nv[f]; ++k) {
+            const double *v1 = pv(P, f, k), *v2 = pv(P, f, k + 1);
+            double a[3] = {v0[0] - g[0], v0[1] - g[1], v0[2] - g[2]};
+            double b[3] = {v1[0] - g[0], v1[1] - g[1], v1[2] - g[2]};
+            double c[3] = {v2[0] - g[0], v2[1] - g[1], v2[2] - g[2]}, bc[3];
+            cross3(b, c, bc);
+            vol += fabs(dot3(a, bc)) / 6.0;
+        }
+    }
+    return vol;
+}
+
+/* Cells of all points.  fptr[n+1] (faces of each cell), vol[n], *nfaces = all
+ * faces; with vptr/verts/labels NULL only the counts are produced.  Otherwise
+ * vptr[nfaces+1] (vertices of each face), verts[3 * total], labels[nfaces].
+ * Returns the total number of face vertices, or a negative error. */
+int64_t orc_cells_3d(int64_t n, const double *x, const double *R, const double *lo, const double *hi,
+                     const int64_t *rowptr, const int32_t *col, int64_t *fptr, int64_t *vptr,
+                     double *verts, int32_t *labels, double *vol, int64_t *nfaces)
+{
+    int64_t maxrow = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] - rowptr[i] > maxrow) maxrow = rowptr[i + 1] - rowptr[i];
+    int cap_f = (int)maxrow + 8, cap_v = (int)maxrow + 16;
+    poly3 P, W;
+    if (poly3_alloc(&P, cap_f, cap_v) || poly3_alloc(&W, cap_f, cap_v)) return ORC_ERR_CAP;
+    double *cut = malloc(sizeof(double) * 6 * (size_t)cap_f * cap_v);
+    int64_t nv_tot = 0, nf_tot = 0;
+    int rc = ORC_OK;
+    fptr[0] = 0;
+    if (vptr) vptr[0] = 0;
+    for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+        const double *xi = x + 3 * i;
+        double b0[3], b1[3];
+        int on_lo[3], on_hi[3];
+        for (int a = 0; a < 3; ++a) {
+            b0[a] = xi[a] - R[i];
+            b1[a] = xi[a] + R[i];
+            on_lo[a] = b0[a] <= lo[a];
+            on_hi[a] = b1[a] >= hi[a];
+            if (on_lo[a]) b0[a] = lo[a];
+            if (on_hi[a]) b1[a] = hi[a];
+        }
+        poly3_box(&P, b0, b1, on_lo, on_hi);
+        double rmax = poly3_rmax(&P, xi);
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1] && rc == ORC_OK; ++p) {
+            int32_t j = col[p];
+            if (j == i) continue;
+            const double *xj = x + 3 * (int64_t)j;
+            double dd[3] = {xj[0] - xi[0], xj[1] - xi[1], xj[2] - xi[2]};
+            if (0.5 * sqrt(dot3(dd, dd)) >= rmax) continue;   /* plane beyond every vertex */
+            rc = poly3_clip(&P, &W, cut, xi, xj, j, 1e-12 * R[i]);
+            rmax = poly3_rmax(&P, xi);
+        }
+        if (rc != ORC_OK) break;
+        if (vol) vol[i] = poly3_volume(&P, xi);
+        for (int f = 0; f < P.nf; ++f) {
+            if (vptr) {
+                vptr[nf_tot + f + 1] = vptr[nf_tot + f] + P.nv[f];
+                labels[nf_tot + f] = P.lab[f];
+                memcpy(verts + 3 * vptr[nf_tot + f], pv(&P, f, 0), sizeof(double) * 3 * P.nv[f]);
+            }
+            nv_tot += P.nv[f];
+        }
+        nf_tot += P.nf;
+        fptr[i + 1] = nf_tot;
+    }
+    poly3_free(&P); poly3_free(&W); free(cut);
+    if (nfaces) *nfaces = nf_tot;
+    return rc == ORC_OK ? nv_tot : rc;
+}
+
+/* Volume points: tetrahedra (x_i, v0, vk, vk+1) of every face fan, reference
+ * rule mapped by x = p0 + (p_a - p0) xi_a (App. A), weight w_ref |det J|. */
+int64_t orc_volume_qps_3d(int64_t n, const double *x, const int64_t *fptr, const int64_t *vptr,
+                          const double *verts, int nref, double *xq, double *wq, int32_t *owner)
+{
+    double xi[3 * 4096], w[4096];
+    if (nref < 1 || nref > 16 || orc_tet_rule(nref, xi, w)) return ORC_ERR_ARG;
+    int nq = nref * nref * nref;
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *g = x + 3 * i;
+        for (int64_t f = fptr[i]; f < fptr[i + 1]; ++f) {
+            int nv = (int)(vptr[f + 1] - vptr[f]);
+            const double *v0 = verts + 3 * vptr[f];
+            for (int k = 1; k + 1 < nv; ++k) {
+                const double *v1 = verts + 3 * (vptr[f] + k), *v2 = verts + 3 * (vptr[f] + k + 1);
+                double e1[3] = {v0[0] - g[0], v0[1] - g[1], v0[2] - g[2]};
+                double e2[3] = {v1[0] - g[0], v1[1] - g[1], v1[2] - g[2]};
+                double e3[3] = {v2[0] - g[0], v2[1] - g[1], v2[2] - g[2]}, c23[3];
+                cross3(e2, e3, c23);
+                double det = fabs(dot3(e1, c23));
+                for (int q = 0; q < nq; ++q) {
+                    if (xq) {
+                        for (int e = 0; e < 3; ++e)
+                            xq[3 * c + e] = g[e] + e1[e] * xi[3 * q] + e2[e] * xi[3 * q + 1] + e3[e] * xi[3 * q + 2];
+                        wq[c] = w[q] * det;
+                        owner[c] = (int32_t)i;
+                    }
+                    ++c;
+                }
+            }
+        }
+    }
+    return c;
+}
+
+/* Boundary points: triangles (v0, vk, vk+1) of every face on the domain
+ * boundary, x = p0 + (p_a - p0) xi_a, weight w_ref |e1 x e2| (App. A). */
+int64_t orc_boundary_qps_3d(int64_t n, const int64_t *fptr, const int64_t *vptr, const double *verts,
+                            const int32_t *labels, int nref, double *xb, double *wb, int32_t *face,
+                            int32_t *owner)
+{
+    double xi[2 * 4096], w[4096];
+    if (nref < 1 || nref > 64 || orc_triangle_rule(nref, xi, w)) return ORC_ERR_ARG;
+    int nq = nref * nref;
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t f = fptr[i]; f < fptr[i + 1]; ++f) {
+            int32_t L = labels[f];
+            if (L >= 0 || L == LABEL_EXTENT) continue;
+            int nv = (int)(vptr[f + 1] - vptr[f]);
+            const double *p0 = verts + 3 * vptr[f];
+            for (int k = 1; k + 1 < nv; ++k) {
+                const double *p1 = verts + 3 * (vptr[f] + k), *p2 = verts + 3 * (vptr[f] + k + 1);
+                double e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
+                double e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]}, cr[3];
+                cross3(e1, e2, cr);
+                double K = sqrt(dot3(cr, cr));
+                for (int q = 0; q < nq; ++q) {
+                    if (xb) {
+                        for (int e = 0; e < 3; ++e) xb[3 * c + e] = p0[e] + e1[e] * xi[2 * q] + e2[e] * xi[2 * q + 1];
+                        wb[c] = w[q] * K;
+                        face[c] = -L - 1;
+                        owner[c] = (int32_t)i;
+                    }
+                    ++c;
+                }
+            }
+        }
+    return c;
+}
+
+/* ======================================================================
  * E. Kernel and reproducing-kernel functions (Sec. 2.1-2.2).
  * ====================================================================== */
 /* cubic spline base kernel, support chi < 2 (normalisation dropped) */
@@ -498,7 +854,7 @@ int64_t orc_rk_at_points(int dim, int64_t n, const double *x, const double *R, c
  * Vectors (each n long, in `vecs`):
  *   Q0 <U_i, q>,  Q^a <d_a U_i, q>,  B_f (U_i, 1) on face f.
  * sigma_t, sigma_s, q are given per volume quadrature point (in the order of
- * orc_volume_qps_2d).  Returns 0 or a negative error.
+ * orc_volume_qps_2d / orc_volume_qps_3d).  Returns 0 or a negative error.
  * ====================================================================== */
 static int64_t find_pos(const int64_t *rowptr, const int32_t *col, int32_t a, int32_t b)
 {
@@ -514,14 +870,14 @@ static int64_t find_pos(const int64_t *rowptr, const int32_t *col, int32_t a, in
 int orc_n_mats(int dim) { return 3 + 3 * dim + dim * dim + 2 * dim; }
 int orc_n_vecs(int dim) { return 1 + dim + 2 * dim; }
 
-int orc_assemble_2d(int64_t n, const double *x, const double *R, const double *V,
-                    const int64_t *rowptr, const int32_t *col, int64_t nvq, const double *xq,
-                    const double *wq, const int32_t *qowner, const double *sig_t_q,
-                    const double *sig_s_q, const double *q_q, int64_t nbq, const double *xb,
-                    const double *wb, const int32_t *bface, const int32_t *bowner, double *mats,
-                    double *vecs)
+int orc_assemble(int dim, int64_t n, const double *x, const double *R, const double *V,
+                 const int64_t *rowptr, const int32_t *col, int64_t nvq, const double *xq,
+                 const double *wq, const int32_t *qowner, const double *sig_t_q,
+                 const double *sig_s_q, const double *q_q, int64_t nbq, const double *xb,
+                 const double *wb, const int32_t *bface, const int32_t *bowner, double *mats,
+                 double *vecs)
 {
-    const int dim = 2;
+    if (dim != 2 && dim != 3) return ORC_ERR_ARG;
     const int64_t nnz = rowptr[n];
     const int nm = orc_n_mats(dim), nvv = orc_n_vecs(dim);
     memset(mats, 0, sizeof(double) * (size_t)nm * nnz);

@@ -81,8 +81,15 @@ def lib():
         L.orc_rk_at_points.restype = i64
         L.orc_n_mats.argtypes = [i32]
         L.orc_n_vecs.argtypes = [i32]
-        L.orc_assemble_2d.argtypes = [i64, P, P, P, P, P, i64, P, P, P, P, P, P, i64, P, P, P, P, P, P]
-        L.orc_assemble_2d.restype = i32
+        L.orc_tet_rule.argtypes = [i32, P, P]
+        L.orc_cells_3d.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P, P]
+        L.orc_cells_3d.restype = i64
+        L.orc_volume_qps_3d.argtypes = [i64, P, P, P, P, i32, P, P, P]
+        L.orc_volume_qps_3d.restype = i64
+        L.orc_boundary_qps_3d.argtypes = [i64, P, P, P, P, i32, P, P, P, P]
+        L.orc_boundary_qps_3d.restype = i64
+        L.orc_assemble.argtypes = [i32, i64, P, P, P, P, P, i64, P, P, P, P, P, P, i64, P, P, P, P, P, P]
+        L.orc_assemble.restype = i32
         _lib = L
     return _lib
 
@@ -110,6 +117,14 @@ def triangle_rule(n):
     xi = np.zeros((n * n, 2))
     w = np.zeros(n * n)
     lib().orc_triangle_rule(n, _p(xi), _p(w))
+    return xi, w
+
+
+def tet_rule(n):
+    xi = np.zeros((n ** 3, 3))
+    w = np.zeros(n ** 3)
+    if lib().orc_tet_rule(n, _p(xi), _p(w)):
+        raise ValueError("bad rule size")
     return xi, w
 
 
@@ -174,6 +189,50 @@ def boundary_qps_2d(n, cptr, verts, labels, nref=5):
     return QP(xb, wb, ow, fc)
 
 
+def cells_3d(x, R, lo, hi, rowptr, col):
+    """Polyhedral Voronoi-like cells (Sec. 3.1).  Returns fptr (faces of each
+    cell), vptr (vertices of each face), verts[nv, 3], labels (per face), V."""
+    x = _c(x, np.float64)
+    n = x.shape[0]
+    lo = _c(lo[:3], np.float64)
+    hi = _c(hi[:3], np.float64)
+    fptr = np.zeros(n + 1, np.int64)
+    vol = np.zeros(n)
+    nf = ctypes.c_int64(0)
+    L = lib()
+    args = (n, _p(x), _p(R), _p(lo), _p(hi), _p(rowptr), _p(col), _p(fptr))
+    nv = L.orc_cells_3d(*args, None, None, None, _p(vol), ctypes.byref(nf))
+    if nv < 0:
+        raise RuntimeError(f"3D cells failed (code {nv})")
+    vptr = np.zeros(nf.value + 1, np.int64)
+    verts = np.zeros((nv, 3))
+    labels = np.zeros(nf.value, np.int32)
+    L.orc_cells_3d(*args, _p(vptr), _p(verts), _p(labels), _p(vol), ctypes.byref(nf))
+    return fptr, vptr, verts, labels, vol
+
+
+def volume_qps_3d(x, fptr, vptr, verts, nref=2):
+    n = x.shape[0]
+    L = lib()
+    c = L.orc_volume_qps_3d(n, _p(x), _p(fptr), _p(vptr), _p(verts), nref, None, None, None)
+    xq = np.zeros((c, 3))
+    wq = np.zeros(c)
+    ow = np.zeros(c, np.int32)
+    L.orc_volume_qps_3d(n, _p(x), _p(fptr), _p(vptr), _p(verts), nref, _p(xq), _p(wq), _p(ow))
+    return QP(xq, wq, ow)
+
+
+def boundary_qps_3d(n, fptr, vptr, verts, labels, nref=2):
+    L = lib()
+    c = L.orc_boundary_qps_3d(n, _p(fptr), _p(vptr), _p(verts), _p(labels), nref, None, None, None, None)
+    xb = np.zeros((c, 3))
+    wb = np.zeros(c)
+    fc = np.zeros(c, np.int32)
+    ow = np.zeros(c, np.int32)
+    L.orc_boundary_qps_3d(n, _p(fptr), _p(vptr), _p(verts), _p(labels), nref, _p(xb), _p(wb), _p(fc), _p(ow))
+    return QP(xb, wb, ow, fc)
+
+
 def rk_at_points(x, R, V, rowptr, col, pts, owner):
     """RK functions U_j and gradients at arbitrary points (Sec. 2.2).
 
@@ -211,20 +270,30 @@ class Discretization:
     """Everything of Sec. 2-3 for one point set: connectivity, cells, volumes,
     quadrature points and the integrated forms of Sec. 4.1."""
 
-    def __init__(self, x, R, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nref_tri=5, nref_line=5):
+    def __init__(self, x, R, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nref_tri=5, nref_line=5,
+                 nref_tet=2, nref_face=2):
+        """2D: 5x5 conical-product triangles (degree 9) and 5-point Gauss-Legendre
+        edges.  3D: 2x2x2 conical-product tetrahedra and 2x2 boundary triangles,
+        degree 3 like the paper's 8-point third-order rule (Sec. 5)."""
         self.x = _c(x, np.float64)
         self.R = _c(R, np.float64)
         self.n, self.dim = self.x.shape
-        if self.dim != 2:
-            raise NotImplementedError("oracle cells are 2D")
+        if self.dim not in (2, 3):
+            raise NotImplementedError("oracle cells are 2D or 3D")
         self.lo = np.asarray(lo, np.float64)
         self.hi = np.asarray(hi, np.float64)
         self.h = 0.5 * self.R                       # smoothing length
         self.rowptr, self.col = neighbors(self.x, self.R)
-        self.cptr, self.verts, self.labels, self.V = cells_2d(
-            self.x, self.R, self.lo, self.hi, self.rowptr, self.col)
-        self.vq = volume_qps_2d(self.x, self.cptr, self.verts, nref_tri)
-        self.bq = boundary_qps_2d(self.n, self.cptr, self.verts, self.labels, nref_line)
+        if self.dim == 2:
+            self.cptr, self.verts, self.labels, self.V = cells_2d(
+                self.x, self.R, self.lo, self.hi, self.rowptr, self.col)
+            self.vq = volume_qps_2d(self.x, self.cptr, self.verts, nref_tri)
+            self.bq = boundary_qps_2d(self.n, self.cptr, self.verts, self.labels, nref_line)
+        else:
+            self.fptr, self.vptr, self.verts, self.labels, self.V = cells_3d(
+                self.x, self.R, self.lo, self.hi, self.rowptr, self.col)
+            self.vq = volume_qps_3d(self.x, self.fptr, self.vptr, self.verts, nref_tet)
+            self.bq = boundary_qps_3d(self.n, self.fptr, self.vptr, self.verts, self.labels, nref_face)
         self.nnz = int(self.rowptr[-1])
 
     # -- integration (Alg. 1) ---------------------------------------------
@@ -236,7 +305,7 @@ class Discretization:
         mats = np.zeros((nm, nnz))
         vecs = np.zeros((nv, n))
         st, ss, qq = (_c(a, np.float64) for a in (sigma_t_q, sigma_s_q, q_q))
-        rc = L.orc_assemble_2d(n, _p(self.x), _p(self.R), _p(self.V), _p(self.rowptr), _p(self.col),
+        rc = L.orc_assemble(d, n, _p(self.x), _p(self.R), _p(self.V), _p(self.rowptr), _p(self.col),
                                len(self.vq.w), _p(self.vq.x), _p(self.vq.w), _p(self.vq.owner),
                                _p(st), _p(ss), _p(qq),
                                len(self.bq.w), _p(self.bq.x), _p(self.bq.w), _p(self.bq.face), _p(self.bq.owner),
