@@ -30,8 +30,9 @@
  *     clipped by the bisector half-planes of every overlap neighbour j != i.
  *   - 2D cells are fanned into triangles (x_i, v_k, v_{k+1}) from the generator,
  *     vertices counter-clockwise; the reference rule is mapped with p0 = x_i.
- *   - 3D cells are fanned into tetrahedra (x_i, f_0, f_k, f_{k+1}) over a fan
- *     of every face f; boundary faces into triangles (f_0, f_k, f_{k+1}).
+ *   - 3D cells are fanned into tetrahedra (x_i, c_f, f_k, f_{k+1}), one per edge
+ *     of every face f, c_f the average of f's vertices; boundary faces into
+ *     triangles (c_f, f_k, f_{k+1}).
  *   - RK basis P_j(x) = [1, (x - x_j)/s] with s = h of the point owning the
  *     evaluation point (any common scale gives the same U in exact arithmetic).
  */
@@ -381,9 +382,10 @@ int64_t orc_boundary_qps_2d(int64_t n, const int64_t *cptr, const double *verts,
  * plane counts as on it (planes through existing edges, vertices or faces, as
  * in unjittered lattices); a plane with no vertex beyond eps cuts nothing.
  * A neighbour whose plane lies beyond the farthest vertex cuts nothing and is
- * skipped.  The cell is split into tetrahedra (x_i, v_0, v_k, v_k+1) from the
- * generator over a fan of every face; boundary faces into triangles
- * (v_0, v_k, v_k+1).
+ * skipped.  Every face is fanned from its centre c_f (the average of its
+ * vertices), so that the split does not depend on where a face's vertex list
+ * starts: the cell into tetrahedra (x_i, c_f, v_k, v_k+1), one per face edge,
+ * and boundary faces into triangles (c_f, v_k, v_k+1).
  * ====================================================================== */
 typedef struct {
     int nf, cap_f, cap_v;
@@ -545,14 +547,24 @@ static int poly3_clip(poly3 *P, poly3 *W, double *cut, const double *xi, const d
     return ORC_OK;
 }
 
-/* volume of a cell: sum of |det(v0 - g, vk - g, vk+1 - g)| / 6 over the fans */
+/* centre of face f: the average of its vertices */
+static void face_centre(const double *v, int nv, double *c)
+{
+    c[0] = c[1] = c[2] = 0.0;
+    for (int k = 0; k < nv; ++k)
+        for (int e = 0; e < 3; ++e) c[e] += v[3 * k + e];
+    for (int e = 0; e < 3; ++e) c[e] /= nv;
+}
+
+/* volume of a cell: sum of |det(c_f - g, vk - g, vk+1 - g)| / 6 over the fans */
 static double poly3_volume(const poly3 *P, const double *g)
 {
     double vol = 0.0;
     for (int f = 0; f < P->nf; ++f) {
-        const double *v0 = pv(P, f, 0);
-        for (int k = 1; k + 1 < P->nv[f]; ++k) {
-            const double *v1 = pv(P, f, k), *v2 = pv(P, f, k + 1);
+        double v0[3];
+        face_centre(pv(P, f, 0), P->nv[f], v0);
+        for (int k = 0; k < P->nv[f]; ++k) {
+            const double *v1 = pv(P, f, k), *v2 = pv(P, f, (k + 1) % P->nv[f]);
             double a[3] = {v0[0] - g[0], v0[1] - g[1], v0[2] - g[2]};
             double b[3] = {v1[0] - g[0], v1[1] - g[1], v1[2] - g[2]};
             double c[3] = {v2[0] - g[0], v2[1] - g[1], v2[2] - g[2]}, bc[3];
@@ -623,7 +635,7 @@ int64_t orc_cells_3d(int64_t n, const double *x, const double *R, const double *
     return rc == ORC_OK ? nv_tot : rc;
 }
 
-/* Volume points: tetrahedra (x_i, v0, vk, vk+1) of every face fan, reference
+/* Volume points: tetrahedra (x_i, c_f, vk, vk+1) of every face fan, reference
  * rule mapped by x = p0 + (p_a - p0) xi_a (App. A), weight w_ref |det J|. */
 int64_t orc_volume_qps_3d(int64_t n, const double *x, const int64_t *fptr, const int64_t *vptr,
                           const double *verts, int nref, double *xq, double *wq, int32_t *owner)
@@ -636,9 +648,10 @@ int64_t orc_volume_qps_3d(int64_t n, const double *x, const int64_t *fptr, const
         const double *g = x + 3 * i;
         for (int64_t f = fptr[i]; f < fptr[i + 1]; ++f) {
             int nv = (int)(vptr[f + 1] - vptr[f]);
-            const double *v0 = verts + 3 * vptr[f];
-            for (int k = 1; k + 1 < nv; ++k) {
-                const double *v1 = verts + 3 * (vptr[f] + k), *v2 = verts + 3 * (vptr[f] + k + 1);
+            double v0[3];
+            face_centre(verts + 3 * vptr[f], nv, v0);
+            for (int k = 0; k < nv; ++k) {
+                const double *v1 = verts + 3 * (vptr[f] + k), *v2 = verts + 3 * (vptr[f] + (k + 1) % nv);
                 double e1[3] = {v0[0] - g[0], v0[1] - g[1], v0[2] - g[2]};
                 double e2[3] = {v1[0] - g[0], v1[1] - g[1], v1[2] - g[2]};
                 double e3[3] = {v2[0] - g[0], v2[1] - g[1], v2[2] - g[2]}, c23[3];
@@ -659,7 +672,7 @@ int64_t orc_volume_qps_3d(int64_t n, const double *x, const int64_t *fptr, const
     return c;
 }
 
-/* Boundary points: triangles (v0, vk, vk+1) of every face on the domain
+/* Boundary points: triangles (c_f, vk, vk+1) of every face on the domain
  * boundary, x = p0 + (p_a - p0) xi_a, weight w_ref |e1 x e2| (App. A). */
 int64_t orc_boundary_qps_3d(int64_t n, const int64_t *fptr, const int64_t *vptr, const double *verts,
                             const int32_t *labels, int nref, double *xb, double *wb, int32_t *face,
@@ -674,9 +687,10 @@ int64_t orc_boundary_qps_3d(int64_t n, const int64_t *fptr, const int64_t *vptr,
             int32_t L = labels[f];
             if (L >= 0 || L == LABEL_EXTENT) continue;
             int nv = (int)(vptr[f + 1] - vptr[f]);
-            const double *p0 = verts + 3 * vptr[f];
-            for (int k = 1; k + 1 < nv; ++k) {
-                const double *p1 = verts + 3 * (vptr[f] + k), *p2 = verts + 3 * (vptr[f] + k + 1);
+            double p0[3];
+            face_centre(verts + 3 * vptr[f], nv, p0);
+            for (int k = 0; k < nv; ++k) {
+                const double *p1 = verts + 3 * (vptr[f] + k), *p2 = verts + 3 * (vptr[f] + (k + 1) % nv);
                 double e1[3] = {p1[0] - p0[0], p1[1] - p0[1], p1[2] - p0[2]};
                 double e2[3] = {p2[0] - p0[0], p2[1] - p0[1], p2[2] - p0[2]}, cr[3];
                 cross3(e1, e2, cr);
