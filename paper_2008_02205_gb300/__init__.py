@@ -279,8 +279,9 @@ class TransportProblem:
     """Owns one context: create -> integrate -> assemble -> step* -> flux."""
 
     def __init__(self, points, kernel_extent, omega, w, sigma_t, sigma_s, q, inflow=None, **options):
-        self.n = int(np.asarray(points).shape[0])
+        self.n, self.dim = (int(v) for v in np.asarray(points).shape)
         self.m = int(np.asarray(omega).shape[0])
+        options.setdefault("dim", self.dim)
         self.opt = mlpg_default_options(**options)
         self.ctx = mlpg_create(self.opt, points, kernel_extent, omega, w, sigma_t, sigma_s, q)
         for f, v in (inflow or {}).items():
@@ -333,7 +334,7 @@ class TransportProblem:
         return mlpg_get_volumes(self.ctx, self.n)
 
     def forms(self):
-        return mlpg_get_forms(self.ctx, self.n, self.stats()["nnz"])
+        return mlpg_get_forms(self.ctx, self.n, self.stats()["nnz"], self.dim)
 
     def close(self):
         if self.ctx:

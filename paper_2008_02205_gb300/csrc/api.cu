@@ -63,7 +63,7 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
     if (!out) return MLPG_ERR_ARG;
     *out = nullptr;
     if (!opt || !points || !extent || !omega || !w || !st || !ss || !q) return MLPG_ERR_ARG;
-    if (opt->dim != 2 || n < 4 || m < 1 || m > MLPG_MAX_DIR) return MLPG_ERR_ARG;
+    if ((opt->dim != 2 && opt->dim != 3) || n < 4 || m < 1 || m > MLPG_MAX_DIR) return MLPG_ERR_ARG;
     if (n >= (int64_t(1) << 31)) return MLPG_ERR_ARG;
     if (opt->inner_restart < 1 || opt->inner_restart > MLPG_MAX_RESTART || opt->outer_restart < 1 ||
         opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART ||
@@ -261,6 +261,37 @@ mlpg_status mlpg_integrate(mlpg_ctx *ctx) {
     GUARD(ctx);
     try {
         MLPG_TRY(run_neighbors(ctx));
+        if (ctx->dim == 3) {
+            HostCells3 c3;
+            int64_t bad = build_cells_3d(ctx->n, ctx->h_x.data(), ctx->h_R.data(), ctx->opt.lo, ctx->opt.hi,
+                                         ctx->h_rowptr.data(), ctx->h_col.data(), c3);
+            if (bad >= 0) return set_err(ctx, MLPG_ERR_GEOMETRY, "empty cell at point " + std::to_string(bad));
+            ctx->ntet = (int64_t)c3.tet_owner.size();
+            ctx->nbtri = (int64_t)c3.tri_owner.size();
+            ctx->nvq = 8 * ctx->ntet;
+            ctx->nbq = 4 * ctx->nbtri;
+            cudaStream_t s = ctx->stream;
+            MLPG_TRY(dalloc(ctx, &ctx->tet_owner, ctx->ntet));
+            MLPG_TRY(dalloc(ctx, &ctx->tet_v, 9 * ctx->ntet));
+            MLPG_TRY(dalloc(ctx, &ctx->tri_owner, ctx->nbtri + 1));
+            MLPG_TRY(dalloc(ctx, &ctx->tri_face, ctx->nbtri + 1));
+            MLPG_TRY(dalloc(ctx, &ctx->tri_v, 9 * ctx->nbtri + 9));
+            CU(ctx, cudaMemcpyAsync(ctx->tet_owner, c3.tet_owner.data(), ctx->ntet * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            CU(ctx, cudaMemcpyAsync(ctx->tet_v, c3.tet_v.data(), 9 * ctx->ntet * sizeof(double), cudaMemcpyHostToDevice, s));
+            if (ctx->nbtri > 0) {
+                CU(ctx, cudaMemcpyAsync(ctx->tri_owner, c3.tri_owner.data(), ctx->nbtri * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->tri_face, c3.tri_face.data(), ctx->nbtri * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+                CU(ctx, cudaMemcpyAsync(ctx->tri_v, c3.tri_v.data(), 9 * ctx->nbtri * sizeof(double), cudaMemcpyHostToDevice, s));
+            }
+            CU(ctx, cudaMemcpyAsync(ctx->V, c3.volume.data(), ctx->n * sizeof(double), cudaMemcpyHostToDevice, s));
+            MLPG_TRY(run_interp_3d(ctx));  // synchronises: the host vectors may go
+            MLPG_TRY(build_blocks(ctx));
+            ctx->st.nnz = ctx->nnz;
+            ctx->st.n_volume_qp = ctx->nvq;
+            ctx->st.n_boundary_qp = ctx->nbq;
+            ctx->state = 1;
+            return MLPG_OK;
+        }
         HostCells cells;
         int64_t bad = build_cells_2d(ctx->n, ctx->h_x.data(), ctx->h_R.data(), ctx->opt.lo, ctx->opt.hi,
                                      ctx->h_rowptr.data(), ctx->h_col.data(), 25, 5, cells);
@@ -292,7 +323,7 @@ mlpg_status mlpg_assemble(mlpg_ctx *ctx) {
     if (ctx->state != 1) return set_err(ctx, MLPG_ERR_STATE, "assemble must follow integrate");
     GUARD(ctx);
     try {
-        MLPG_TRY(run_assemble(ctx));
+        MLPG_TRY(ctx->dim == 3 ? run_assemble_3d(ctx) : run_assemble(ctx));
         ctx->kappa = -1.0;
         ctx->state = 2;
         return MLPG_OK;
@@ -378,9 +409,10 @@ mlpg_status mlpg_get_stats(const mlpg_ctx *cctx, mlpg_stats *st) {
     GUARD(ctx);
     if (ctx->timing) harvest_timing(ctx);
     // algorithmic bytes of one batched L-apply
-    const int64_t nnz = ctx->nnz, n = ctx->n, m = ctx->m;
+    const int64_t nnz = ctx->nnz, n = ctx->n, m = ctx->m, d = ctx->dim;
+    const int64_t na = 1 + d + d * (d + 1) / 2, nf = 2 * d;   // base arrays, faces
     if (ctx->opt.precision == MLPG_MIXED)
-        ctx->st.spmm_bytes = nnz * (4 + 6 * 4) + ctx->nb * (4 + 4 * 4) + 2 * 4 * (n + 1) + 2 * n * m * 4;
+        ctx->st.spmm_bytes = nnz * (4 + na * 4) + ctx->nb * (4 + nf * 4) + 2 * 4 * (n + 1) + 2 * n * m * 4;
     else
         ctx->st.spmm_bytes = nnz * (4 + 8 * m) + 4 * (n + 1) + 2 * n * m * 8;
     *st = ctx->st;

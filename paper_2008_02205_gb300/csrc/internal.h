@@ -49,9 +49,22 @@ constexpr int32_t kLabelExtent = -100;
 int64_t build_cells_2d(int64_t n, const double *x, const double *R, const double *lo,
                        const double *hi, const int32_t *rowptr, const int32_t *col,
                        int tri_points, int line_points, HostCells &out);
+// 3D cells as flat element lists: tetrahedra (generator of `owner`, three
+// stored vertices) and boundary triangles (three stored vertices, box face).
+struct HostCells3 {
+    std::vector<double> volume;      // n
+    std::vector<int32_t> tet_owner;  // ntet
+    std::vector<double> tet_v;       // 9 * ntet
+    std::vector<int32_t> tri_owner;  // ntri
+    std::vector<int32_t> tri_face;   // ntri: 0..5 = -x, +x, -y, +y, -z, +z
+    std::vector<double> tri_v;       // 9 * ntri
+};
+int64_t build_cells_3d(int64_t n, const double *x, const double *R, const double *lo,
+                       const double *hi, const int32_t *rowptr, const int32_t *col, HostCells3 &out);
 // Reference rules (quadrature.cpp).
 void gauss_jacobi_newton(int n, double a, double b, double *t, double *w);
 void triangle_rule(int n1d, double *xi /*2*n1d^2*/, double *w);
+void tet_rule(int n1d, double *xi /*3*n1d^3*/, double *w);
 void line_rule(int n, double *t, double *w);
 
 // GMRES workspace ------------------------------------------------------------
@@ -111,6 +124,10 @@ struct mlpg_ctx {
     int64_t nverts = 0, nvq = 0, nbq = 0;
     int32_t *cptr = nullptr, *labels = nullptr;
     double *verts = nullptr;
+    // 3D cells as elements: tetrahedra and boundary triangles (HostCells3)
+    int64_t ntet = 0, nbtri = 0;
+    int32_t *tet_owner = nullptr, *tri_owner = nullptr, *tri_face = nullptr;
+    double *tet_v = nullptr, *tri_v = nullptr;
     double *interp = nullptr;   // [nnz]: V_j U_j(x_i) on the overlap pattern
     int *d_flag = nullptr;      // device error flag (assembly / RK)
 
@@ -197,6 +214,8 @@ mlpg_status dalloc(mlpg_ctx *ctx, T **p, size_t count) {
 mlpg_status run_neighbors(mlpg_ctx *ctx);
 mlpg_status run_interp(mlpg_ctx *ctx);
 mlpg_status run_assemble(mlpg_ctx *ctx);
+mlpg_status run_interp_3d(mlpg_ctx *ctx);
+mlpg_status run_assemble_3d(mlpg_ctx *ctx);
 mlpg_status form_operators(mlpg_ctx *ctx, double kappa);
 mlpg_status apply_L64(mlpg_ctx *ctx, const double *X, double *Y);
 mlpg_status apply_L32(mlpg_ctx *ctx, const float *X, float *Y);

@@ -36,6 +36,26 @@ __global__ void k_rowidx(int64_t n, const int32_t *__restrict__ rowptr, int32_t 
     for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) rowidx[p] = (int32_t)i;
 }
 
+// Dimension-dependent layout (D = 2 or 3).
+//   base arrays of L (NA): 1, Omega_a (D), Omega_a^2 (D), Omega_a Omega_b (a < b)
+//   T and MS arrays (NT = 1 + D): M0 / Ms and tau G^a / tau Gs^a
+//   faces (NF = 2D): -x, +x, -y, +y (, -z, +z)
+//   mats: 0 M0, 1 Mt, 2 Ms, 3 G, 3+D Gt, 3+2D Gs, 3+3D K (a-major), 3+3D+D^2 S_f
+//   vecs: 0 Q0, 1 Q, 1+D B_f
+//   coef (double, stride kCS): the NA coefficients of a direction; fcoef
+//   (stride kFS): outflow coefficients max(Omega . n_f, 0); coef32 (float,
+//   stride 16): the NA coefficients, the faces from slot face_slot<D>().
+template <int D> __host__ __device__ constexpr int NA() { return 1 + D + D * (D + 1) / 2; }
+template <int D> __host__ __device__ constexpr int NT() { return 1 + D; }
+template <int D> __host__ __device__ constexpr int NF() { return 2 * D; }
+template <int D> __host__ __device__ constexpr int face_slot() { return D == 2 ? 8 : 10; }
+template <int D> __host__ __device__ constexpr int mat_S() { return 3 + 3 * D + D * D; }
+constexpr int kCS = 16, kFS = 8;
+struct Inflow {
+    double v[6];
+};
+
+template <int D>
 __global__ void k_form_arrays(int64_t nnz, double kappa, const int32_t *__restrict__ rowidx,
                               const double *__restrict__ tau, const double *__restrict__ mats,
                               double *__restrict__ A64, float *__restrict__ A32,
@@ -44,49 +64,63 @@ __global__ void k_form_arrays(int64_t nnz, double kappa, const int32_t *__restri
     if (p >= nnz) return;
     const double t = tau[rowidx[p]];
     const double *M0 = mats, *Mt = mats + nnz, *Ms = mats + 2 * nnz;
-    const double *Gx = mats + 3 * nnz, *Gy = mats + 4 * nnz, *Gtx = mats + 5 * nnz,
-                 *Gty = mats + 6 * nnz, *Gsx = mats + 7 * nnz, *Gsy = mats + 8 * nnz;
-    const double *Kxx = mats + 9 * nnz, *Kxy = mats + 10 * nnz, *Kyx = mats + 11 * nnz,
-                 *Kyy = mats + 12 * nnz;
-    double a[6];
+    const double *G = mats + 3 * nnz, *Gt = mats + (3 + D) * nnz, *Gs = mats + (3 + 2 * D) * nnz;
+    const double *K = mats + (3 + 3 * D) * nnz;
+    double a[NA<D>()];
     a[0] = kappa * M0[p] + Mt[p];
-    a[1] = (kappa * t - 1.0) * Gx[p] + t * Gtx[p];
-    a[2] = (kappa * t - 1.0) * Gy[p] + t * Gty[p];
-    a[3] = t * Kxx[p];
-    a[4] = t * Kyy[p];
-    a[5] = t * (Kxy[p] + Kyx[p]);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        A64[k * nnz + p] = a[k];
-        A32[k * nnz + p] = (float)a[k];
+    for (int c = 0; c < D; ++c) {
+        a[1 + c] = (kappa * t - 1.0) * G[c * nnz + p] + t * Gt[c * nnz + p];
+        a[1 + D + c] = t * K[(c * D + c) * nnz + p];
+    }
+    int k = 1 + 2 * D;
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+        for (int e = c + 1; e < D; ++e) a[k++] = t * (K[(c * D + e) * nnz + p] + K[(e * D + c) * nnz + p]);
+#pragma unroll
+    for (int k2 = 0; k2 < NA<D>(); ++k2) {
+        A64[k2 * nnz + p] = a[k2];
+        A32[k2 * nnz + p] = (float)a[k2];
     }
     T64[p] = kappa * M0[p];
-    T64[nnz + p] = kappa * t * Gx[p];
-    T64[2 * nnz + p] = kappa * t * Gy[p];
     S64[p] = Ms[p];
-    S64[nnz + p] = t * Gsx[p];
-    S64[2 * nnz + p] = t * Gsy[p];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        T64[(1 + c) * nnz + p] = kappa * t * G[c * nnz + p];
+        S64[(1 + c) * nnz + p] = t * Gs[c * nnz + p];
+    }
 }
 
+template <int D>
 __global__ void k_coef(int m, const double *__restrict__ omega, double *__restrict__ coef,
                        double *__restrict__ fcoef, float *__restrict__ coef32) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m) return;
-    double ox = omega[3 * k], oy = omega[3 * k + 1];
-    double *c = coef + 8 * k;
-    c[0] = 1.0; c[1] = ox; c[2] = oy; c[3] = ox * ox; c[4] = oy * oy; c[5] = ox * oy; c[6] = 0; c[7] = 0;
-    // faces -x, +x, -y, +y: outward normals; outflow coefficient max(Omega . n, 0)
-    fcoef[4 * k + 0] = fmax(-ox, 0.0);
-    fcoef[4 * k + 1] = fmax(ox, 0.0);
-    fcoef[4 * k + 2] = fmax(-oy, 0.0);
-    fcoef[4 * k + 3] = fmax(oy, 0.0);
-    // float copy for the FP32 kernels: [k][0..7] = 1, c1..c5, 0, 0 and the faces at [k][8..11]
+    const double o[3] = {omega[3 * k], omega[3 * k + 1], omega[3 * k + 2]};
+    double *c = coef + kCS * k;
+    for (int q = 0; q < kCS; ++q) c[q] = 0.0;
+    c[0] = 1.0;
+    for (int a = 0; a < D; ++a) {
+        c[1 + a] = o[a];
+        c[1 + D + a] = o[a] * o[a];
+    }
+    int q = 1 + 2 * D;
+    for (int a = 0; a < D; ++a)
+        for (int b = a + 1; b < D; ++b) c[q++] = o[a] * o[b];
+    // faces with outward normals -e_a, +e_a: outflow coefficient max(Omega . n, 0)
+    for (int f = 0; f < kFS; ++f) fcoef[kFS * k + f] = 0.0;
+    for (int a = 0; a < D; ++a) {
+        fcoef[kFS * k + 2 * a] = fmax(-o[a], 0.0);
+        fcoef[kFS * k + 2 * a + 1] = fmax(o[a], 0.0);
+    }
     float *c32 = coef32 + 16 * k;
-    for (int q = 0; q < 8; ++q) c32[q] = (float)c[q];
-    for (int f = 0; f < 4; ++f) c32[8 + f] = (float)fcoef[4 * k + f];
-    for (int q = 12; q < 16; ++q) c32[q] = 0.0f;
+    for (int q2 = 0; q2 < 16; ++q2) c32[q2] = 0.0f;
+    for (int q2 = 0; q2 < NA<D>(); ++q2) c32[q2] = (float)c[q2];
+    for (int f = 0; f < NF<D>(); ++f) c32[face_slot<D>() + f] = (float)fcoef[kFS * k + f];
 }
 
+template <int D>
 __global__ void k_materialize(int64_t nnz, int m, const double *__restrict__ A64,
                               const double *__restrict__ Sf, const double *__restrict__ coef,
                               const double *__restrict__ fcoef, double *__restrict__ L64) {
@@ -94,47 +128,49 @@ __global__ void k_materialize(int64_t nnz, int m, const double *__restrict__ A64
     if (e >= nnz * m) return;
     int64_t p = e / m;
     int k = (int)(e - p * m);
-    const double *c = coef + 8 * k, *fc = fcoef + 4 * k;
+    const double *c = coef + kCS * k, *fc = fcoef + kFS * k;
     double v = A64[p];
 #pragma unroll
-    for (int j = 1; j < 6; ++j) v += c[j] * A64[j * nnz + p];
+    for (int j = 1; j < NA<D>(); ++j) v += c[j] * A64[j * nnz + p];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) v += fc[f] * Sf[f * nnz + p];
+    for (int f = 0; f < NF<D>(); ++f) v += fc[f] * Sf[f * nnz + p];
     L64[e] = v;
 }
 
+template <int D>
 __global__ void k_diag_rhs(int64_t n, int m, const int32_t *__restrict__ diag, int64_t nnz,
                            const double *__restrict__ A64, const double *__restrict__ Sf,
                            const double *__restrict__ coef, const double *__restrict__ fcoef,
                            const double *__restrict__ tau, const double *__restrict__ vecs,
-                           double4 psib, double *__restrict__ dinv64, float *__restrict__ dinv32,
+                           Inflow psib, double *__restrict__ dinv64, float *__restrict__ dinv32,
                            double *__restrict__ r64, int *__restrict__ flag) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * m) return;
     int64_t i = e / m;
     int k = (int)(e - i * m);
-    const double *c = coef + 8 * k, *fc = fcoef + 4 * k;
+    const double *c = coef + kCS * k, *fc = fcoef + kFS * k;
     int32_t p = diag[i];
     double d = A64[p];
-    for (int j = 1; j < 6; ++j) d += c[j] * A64[j * nnz + p];
-    for (int f = 0; f < 4; ++f) d += fc[f] * Sf[f * nnz + p];
+    for (int j = 1; j < NA<D>(); ++j) d += c[j] * A64[j * nnz + p];
+    for (int f = 0; f < NF<D>(); ++f) d += fc[f] * Sf[f * nnz + p];
     if (!(fabs(d) > 0.0)) {
         atomicOr(flag, 16);
         d = 1.0;
     }
     dinv64[e] = 1.0 / d;
     dinv32[e] = (float)(1.0 / d);
-    const double *Q0 = vecs, *Qx = vecs + n, *Qy = vecs + 2 * n, *B = vecs + 3 * n;
-    double ox = c[1], oy = c[2];
-    double r = Q0[i] + tau[i] * (ox * Qx[i] + oy * Qy[i]);
-    // inflow faces: Omega . n_f < 0, coefficient |Omega . n_f| = max(-Omega . n_f, 0)
-    double pb[4] = {psib.x, psib.y, psib.z, psib.w};
-    double inc[4] = {fmax(ox, 0.0), fmax(-ox, 0.0), fmax(oy, 0.0), fmax(-oy, 0.0)};
-    for (int f = 0; f < 4; ++f) r += inc[f] * pb[f] * B[f * n + i];
+    const double *Q0 = vecs, *Q = vecs + n, *B = vecs + (1 + D) * n;
+    double qa = 0.0;
+    for (int a = 0; a < D; ++a) qa += c[1 + a] * Q[a * n + i];
+    double r = Q0[i] + tau[i] * qa;
+    // inflow faces: Omega . n_f < 0, coefficient |Omega . n_f| (the outflow
+    // coefficient of the opposite face)
+    for (int f = 0; f < NF<D>(); ++f) r += fc[f ^ 1] * psib.v[f] * B[f * n + i];
     r64[e] = r;
 }
 
 // boundary segment: entries of rows that touch a face (S_f != 0)
+template <int D>
 __global__ void k_bcount(int64_t n, const int32_t *__restrict__ rowptr, int64_t nnz,
                          const double *__restrict__ Sf, int *__restrict__ cnt) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -142,12 +178,13 @@ __global__ void k_bcount(int64_t n, const int32_t *__restrict__ rowptr, int64_t 
     int c = 0;
     for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
         bool nz = false;
-        for (int f = 0; f < 4; ++f) nz |= Sf[f * nnz + p] != 0.0;
+        for (int f = 0; f < NF<D>(); ++f) nz |= Sf[f * nnz + p] != 0.0;
         c += nz;
     }
     cnt[i] = c;
 }
 
+template <int D>
 __global__ void k_bfill(int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
                         int64_t nnz, const double *__restrict__ Sf, const int32_t *__restrict__ bptr,
                         int64_t nb, int32_t *__restrict__ bcol, double *__restrict__ bval64,
@@ -157,10 +194,10 @@ __global__ void k_bfill(int64_t n, const int32_t *__restrict__ rowptr, const int
     int32_t o = bptr[i];
     for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
         bool nz = false;
-        for (int f = 0; f < 4; ++f) nz |= Sf[f * nnz + p] != 0.0;
+        for (int f = 0; f < NF<D>(); ++f) nz |= Sf[f * nnz + p] != 0.0;
         if (!nz) continue;
         bcol[o] = col[p];
-        for (int f = 0; f < 4; ++f) {
+        for (int f = 0; f < NF<D>(); ++f) {
             bval64[f * nb + o] = Sf[f * nnz + p];
             bval32[f * nb + o] = (float)Sf[f * nnz + p];
         }
@@ -263,7 +300,7 @@ __global__ void __launch_bounds__(256) k_spmm64(int64_t n, int m, int tm_log2,
 // outflow-face terms of the few boundary rows are added by k_faces32 (kept
 // out of this loop: a second loop here slows the main one down by half).
 // IDX is the index type of the [n][m] vectors (int when n * m < 2^31).
-template <int DPL, bool EXACT, typename IDX>
+template <int DPL, bool EXACT, typename IDX, int D>
 __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, int64_t nnz,
                                                 const int32_t *__restrict__ rowptr,
                                                 const int32_t *__restrict__ col,
@@ -271,50 +308,57 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
                                                 const float *__restrict__ coef32,
                                                 const float *__restrict__ X, const float *__restrict__ B,
                                                 float *__restrict__ Y) {
+    constexpr int K = NA<D>();
     const int TM = 1 << tm_log2;
     const int lane = threadIdx.x & (TM - 1);
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
     if (row >= n) return;
-    float c1[DPL], c2[DPL], c3[DPL], c4[DPL], c5[DPL], acc[DPL];
+    float c[K][DPL], acc[DPL];
     bool on[DPL];
 #pragma unroll
     for (int t = 0; t < DPL; ++t) {
         int k = lane + t * TM;
         on[t] = EXACT || k < m;
         k = on[t] ? k : m - 1;
-        c1[t] = coef32[16 * k + 1];
-        c2[t] = coef32[16 * k + 2];
-        c3[t] = coef32[16 * k + 3];
-        c4[t] = coef32[16 * k + 4];
-        c5[t] = coef32[16 * k + 5];
+#pragma unroll
+        for (int q = 1; q < K; ++q) c[q][t] = coef32[16 * k + q];
         acc[t] = 0.0f;
     }
     const int32_t p1 = rowptr[row + 1];
     int32_t p = rowptr[row];
     for (; p + 1 < p1; p += 2) {   // two entries in flight
         const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)lane, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)lane;
-        const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
-                    a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
-        const float b0 = A32[p + 1], b1 = A32[nnz + p + 1], b2 = A32[2 * nnz + p + 1], b3 = A32[3 * nnz + p + 1],
-                    b4 = A32[4 * nnz + p + 1], b5 = A32[5 * nnz + p + 1];
+        float a[K], b[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            a[q] = A32[q * nnz + p];
+            b[q] = A32[q * nnz + p + 1];
+        }
 #pragma unroll
         for (int t = 0; t < DPL; ++t) {
             if (on[t]) {
                 const float x0 = X[jb0 + t * TM], x1 = X[jb1 + t * TM];
-                float v0 = fmaf(c5[t], a5, fmaf(c4[t], a4, fmaf(c3[t], a3, fmaf(c2[t], a2, fmaf(c1[t], a1, a0)))));
-                float v1 = fmaf(c5[t], b5, fmaf(c4[t], b4, fmaf(c3[t], b3, fmaf(c2[t], b2, fmaf(c1[t], b1, b0)))));
+                float v0 = a[0], v1 = b[0];
+#pragma unroll
+                for (int q = 1; q < K; ++q) {
+                    v0 = fmaf(c[q][t], a[q], v0);
+                    v1 = fmaf(c[q][t], b[q], v1);
+                }
                 acc[t] = fmaf(v1, x1, fmaf(v0, x0, acc[t]));
             }
         }
     }
     for (; p < p1; ++p) {
         const IDX jb = (IDX)col[p] * (IDX)m + (IDX)lane;
-        const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
-                    a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
+        float a[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) a[q] = A32[q * nnz + p];
 #pragma unroll
         for (int t = 0; t < DPL; ++t) {
             if (on[t]) {
-                float v = fmaf(c5[t], a5, fmaf(c4[t], a4, fmaf(c3[t], a3, fmaf(c2[t], a2, fmaf(c1[t], a1, a0)))));
+                float v = a[0];
+#pragma unroll
+                for (int q = 1; q < K; ++q) v = fmaf(c[q][t], a[q], v);
                 acc[t] = fmaf(v, X[jb + t * TM], acc[t]);
             }
         }
@@ -333,7 +377,7 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
 // rows, subtracted from (residual form) or added to Y.  One warp per row of
 // the boundary-row list: 32 / TM entry slots x TM direction lanes, slot sums
 // combined with shuffles.
-template <int DPL>
+template <int DPL, int D>
 __global__ void __launch_bounds__(256) k_faces32(int64_t nbr, int m, int tm_log2, int64_t nb,
                                                  const int32_t *__restrict__ brow,
                                                  const int32_t *__restrict__ bptr,
@@ -352,13 +396,17 @@ __global__ void __launch_bounds__(256) k_faces32(int64_t nbr, int m, int tm_log2
     for (int t = 0; t < DPL; ++t) acc[t] = 0.0f;
     for (int32_t q = bptr[row] + slot; q < bptr[row + 1]; q += S) {
         const int64_t jb = (int64_t)bcol[q] * m + lane;
-        const float s0 = bval[q], s1 = bval[nb + q], s2 = bval[2 * nb + q], s3 = bval[3 * nb + q];
+        float sv[NF<D>()];
+#pragma unroll
+        for (int f = 0; f < NF<D>(); ++f) sv[f] = bval[f * nb + q];
 #pragma unroll
         for (int t = 0; t < DPL; ++t) {
             int k = lane + t * TM;
             if (k < m) {
-                const float *fc = coef32 + 16 * k + 8;
-                float v = fmaf(fc[0], s0, fmaf(fc[1], s1, fmaf(fc[2], s2, fc[3] * s3)));
+                const float *fc = coef32 + 16 * k + face_slot<D>();
+                float v = fc[NF<D>() - 1] * sv[NF<D>() - 1];
+#pragma unroll
+                for (int f = NF<D>() - 2; f >= 0; --f) v = fmaf(fc[f], sv[f], v);
                 acc[t] = fmaf(v, X[jb + t * TM], acc[t]);
             }
         }
@@ -382,8 +430,8 @@ __global__ void k_brows(int64_t n, const int32_t *__restrict__ bptr, int32_t *__
     if (bptr[i + 1] > bptr[i]) brow[atomicAdd(count, 1)] = (int32_t)i;
 }
 
-// RHS f[i][m] = (T_m X)_i + r[i][m] with T_m = T0 + Omega^x Tx + Omega^y Ty (FP64).
-template <int DPL>
+// RHS f[i][m] = (T_m X)_i + r[i][m] with T_m = T0 + sum_a Omega^a T_a (FP64).
+template <int DPL, int D>
 __global__ void __launch_bounds__(256) k_rhs64(int64_t n, int m, int tm_log2, int64_t nnz,
                                                const int32_t *__restrict__ rowptr,
                                                const int32_t *__restrict__ col,
@@ -395,22 +443,29 @@ __global__ void __launch_bounds__(256) k_rhs64(int64_t n, int m, int tm_log2, in
     const int lane = threadIdx.x & (TM - 1);
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
     if (row >= n) return;
-    double acc[DPL], cx[DPL], cy[DPL];
+    double acc[DPL], cw[D][DPL];
 #pragma unroll
     for (int t = 0; t < DPL; ++t) {
         int k = lane + t * TM;
         k = k < m ? k : m - 1;
-        cx[t] = coef[8 * k + 1];
-        cy[t] = coef[8 * k + 2];
+#pragma unroll
+        for (int a = 0; a < D; ++a) cw[a][t] = coef[kCS * k + 1 + a];
         acc[t] = 0.0;
     }
     for (int32_t p = rowptr[row]; p < rowptr[row + 1]; ++p) {
         const int64_t j = col[p];
-        const double t0 = T64[p], tx = T64[nnz + p], ty = T64[2 * nnz + p];
+        double tv[NT<D>()];
+#pragma unroll
+        for (int a = 0; a < NT<D>(); ++a) tv[a] = T64[a * nnz + p];
 #pragma unroll
         for (int t = 0; t < DPL; ++t) {
             int k = lane + t * TM;
-            if (k < m) acc[t] = fma(fma(cy[t], ty, fma(cx[t], tx, t0)), X[j * m + k], acc[t]);
+            if (k < m) {
+                double v = tv[0];
+#pragma unroll
+                for (int a = 0; a < D; ++a) v = fma(cw[a][t], tv[1 + a], v);
+                acc[t] = fma(v, X[j * m + k], acc[t]);
+            }
         }
     }
 #pragma unroll
@@ -420,48 +475,55 @@ __global__ void __launch_bounds__(256) k_rhs64(int64_t n, int m, int tm_log2, in
     }
 }
 
-// a = Ms Phi, bx = tau Gs^x Phi, by = tau Gs^y Phi (three SpMVs on one vector)
+// abc[0] = Ms Phi, abc[1 + a] = tau Gs^a Phi (1 + D SpMVs on one vector)
+template <int D>
 __global__ void k_ms_spmv(int64_t n, int64_t nnz, const int32_t *__restrict__ rowptr,
                           const int32_t *__restrict__ col, const double *__restrict__ S64,
                           const double *__restrict__ phi, double *__restrict__ abc) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double a = 0, bx = 0, by = 0;
+    double acc[NT<D>()];
+#pragma unroll
+    for (int a = 0; a < NT<D>(); ++a) acc[a] = 0.0;
     for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
         double v = phi[col[p]];
-        a = fma(S64[p], v, a);
-        bx = fma(S64[nnz + p], v, bx);
-        by = fma(S64[2 * nnz + p], v, by);
+#pragma unroll
+        for (int a = 0; a < NT<D>(); ++a) acc[a] = fma(S64[a * nnz + p], v, acc[a]);
     }
-    abc[i] = a;
-    abc[n + i] = bx;
-    abc[2 * n + i] = by;
+#pragma unroll
+    for (int a = 0; a < NT<D>(); ++a) abc[a * n + i] = acc[a];
 }
 
-template <typename T>
+template <typename T, int D>
 __global__ void k_ms_expand(int64_t n, int m, const double *__restrict__ abc,
                             const double *__restrict__ coef, T *__restrict__ out) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * m) return;
     int64_t i = e / m;
     int k = (int)(e - i * m);
-    double v = (abc[i] + coef[8 * k + 1] * abc[n + i] + coef[8 * k + 2] * abc[2 * n + i]) / kFourPi;
-    out[e] = (T)v;
+    double v = abc[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) v = v + coef[kCS * k + 1 + a] * abc[(1 + a) * n + i];
+    out[e] = (T)(v / kFourPi);
 }
 
-// FP32 variant: the three per-point products arrive pre-scaled by 1/(4 pi) in float
+// FP32 variant: the per-point products arrive pre-scaled by 1/(4 pi) in float
+template <int D>
 __global__ void k_ms_expand32(int64_t n, int m, const float *__restrict__ abc32,
                               const float *__restrict__ coef32, float *__restrict__ out) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n * m) return;
     int64_t i = e / m;
     int k = (int)(e - i * m);
-    out[e] = fmaf(coef32[16 * k + 2], abc32[2 * n + i], fmaf(coef32[16 * k + 1], abc32[n + i], abc32[i]));
+    float v = abc32[i];
+#pragma unroll
+    for (int a = 0; a < D; ++a) v = fmaf(coef32[16 * k + 1 + a], abc32[(1 + a) * n + i], v);
+    out[e] = v;
 }
 
-__global__ void k_abc32(int64_t n, const double *__restrict__ abc, float *__restrict__ abc32) {
+__global__ void k_abc32(int64_t cnt, const double *__restrict__ abc, float *__restrict__ abc32) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= 3 * n) return;
+    if (i >= cnt) return;
     abc32[i] = (float)(abc[i] / kFourPi);
 }
 
@@ -485,6 +547,7 @@ __global__ void k_interp_apply(int64_t n, const int32_t *__restrict__ rowptr, co
 // ---------------------------------------------------------------------------
 constexpr int kB = MLPG_BLOCK_PTS;
 
+template <int D>
 __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const int32_t *__restrict__ rowptr,
                                                    const int32_t *__restrict__ col, int64_t nnz,
                                                    const double *__restrict__ A64, const double *__restrict__ Sf,
@@ -499,7 +562,7 @@ __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const in
     const int dir = blockIdx.y * 8 + warp;
     if (dir >= m) return;
     float(*A)[2 * kB + 1] = sA[warp];
-    const double *c = coef + 8 * dir, *fc = fcoef + 4 * dir;
+    const double *c = coef + kCS * dir, *fc = fcoef + kFS * dir;
     if (lane < kB) {
         const int a = lane;
         for (int b = 0; b < 2 * kB; ++b) A[a][b] = (b == kB + a) ? 1.0f : 0.0f;
@@ -511,8 +574,8 @@ __global__ void __launch_bounds__(256) k_block_inv(int64_t nblk, int m, const in
                 int32_t sl = bof[col[p]];
                 if (sl / kB != k) continue;
                 double v = A64[p];
-                for (int q = 1; q < 6; ++q) v += c[q] * A64[q * nnz + p];
-                for (int f = 0; f < 4; ++f) v += fc[f] * Sf[f * nnz + p];
+                for (int q = 1; q < NA<D>(); ++q) v += c[q] * A64[q * nnz + p];
+                for (int f = 0; f < NF<D>(); ++f) v += fc[f] * Sf[f * nnz + p];
                 A[a][sl - k * kB] = (float)v;
             }
         }
@@ -761,25 +824,27 @@ Team pick_team(int m) {
 static int64_t team_grid(int64_t n, const Team &) { return (n * 32 + 255) / 256; }
 static int64_t rowteam_grid(int64_t n, const Team &tm) { return ((n << tm.tm_log2) + 255) / 256; }
 
-static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
+template <int D>
+static mlpg_status init_operator_storage_d(mlpg_ctx *ctx) {
     const int64_t n = ctx->n, nnz = ctx->nnz;
     const int m = ctx->m;
     cudaStream_t s = ctx->stream;
     MLPG_TRY(dalloc(ctx, &ctx->rowidx, nnz));
     k_rowidx<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, ctx->rowidx);
     CU_LAUNCH(ctx);
-    MLPG_TRY(dalloc(ctx, &ctx->A64, 6 * nnz));
-    MLPG_TRY(dalloc(ctx, &ctx->A32, 6 * nnz));
-    MLPG_TRY(dalloc(ctx, &ctx->T64, 3 * nnz));
-    MLPG_TRY(dalloc(ctx, &ctx->S64, 3 * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->A64, NA<D>() * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->A32, NA<D>() * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->T64, NT<D>() * nnz));
+    MLPG_TRY(dalloc(ctx, &ctx->S64, NT<D>() * nnz));
     MLPG_TRY(dalloc(ctx, &ctx->L64, (size_t)nnz * m));
-    MLPG_TRY(dalloc(ctx, &ctx->coef, 8 * m));
-    MLPG_TRY(dalloc(ctx, &ctx->fcoef, 4 * m));
+    MLPG_TRY(dalloc(ctx, &ctx->coef, kCS * m));
+    MLPG_TRY(dalloc(ctx, &ctx->fcoef, kFS * m));
     MLPG_TRY(dalloc(ctx, &ctx->coef32, 16 * m));
     MLPG_TRY(dalloc(ctx, &ctx->dinv64, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->dinv32, (size_t)n * m));
     MLPG_TRY(dalloc(ctx, &ctx->r64, (size_t)n * m));
-    MLPG_TRY(dalloc(ctx, &ctx->abc, 5 * n));   // [3][n] FP64 products + [3][n] float copy
+    // [NT][n] FP64 products + [NT][n] float copy
+    MLPG_TRY(dalloc(ctx, &ctx->abc, (NT<D>() + (NT<D>() + 1) / 2) * n));
     MLPG_TRY(dalloc(ctx, &ctx->Pinv, (size_t)ctx->nblk * kB * kB * m));
     if (ctx->opt.precision == MLPG_MIXED && ctx->opt.mixed_half_prec && (m & 3) == 0) {
         MLPG_TRY(dalloc(ctx, &ctx->Pinv16, (size_t)ctx->nblk * kB * kB * m));
@@ -789,8 +854,8 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     int *cnt;
     MLPG_TRY(dalloc(ctx, &cnt, n));
     MLPG_TRY(dalloc(ctx, &ctx->bptr, n + 1));
-    const double *Sf = ctx->mats + 13 * nnz;
-    k_bcount<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, nnz, Sf, cnt);
+    const double *Sf = ctx->mats + mat_S<D>() * nnz;
+    k_bcount<D><<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, nnz, Sf, cnt);
     CU_LAUNCH(ctx);
     k_scan1<<<1, 1024, 0, s>>>(n, cnt, ctx->bptr);
     CU_LAUNCH(ctx);
@@ -799,9 +864,9 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     CU(ctx, cudaStreamSynchronize(s));
     ctx->nb = nb32;
     MLPG_TRY(dalloc(ctx, &ctx->bcol, ctx->nb));
-    MLPG_TRY(dalloc(ctx, &ctx->bval64, 4 * ctx->nb));
-    MLPG_TRY(dalloc(ctx, &ctx->bval32, 4 * ctx->nb));
-    k_bfill<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, ctx->col, nnz, Sf, ctx->bptr, ctx->nb,
+    MLPG_TRY(dalloc(ctx, &ctx->bval64, NF<D>() * ctx->nb));
+    MLPG_TRY(dalloc(ctx, &ctx->bval32, NF<D>() * ctx->nb));
+    k_bfill<D><<<(n + 255) / 256, 256, 0, s>>>(n, ctx->rowptr, ctx->col, nnz, Sf, ctx->bptr, ctx->nb,
                                             ctx->bcol, ctx->bval64, ctx->bval32);
     CU_LAUNCH(ctx);
     // list of the rows that have face terms
@@ -815,27 +880,33 @@ static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
     CU(ctx, cudaMemcpyAsync(&nbr, bcount, sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(ctx, cudaStreamSynchronize(s));
     ctx->nbrow = nbr;
-    k_coef<<<(m + 127) / 128, 128, 0, s>>>(m, ctx->omega, ctx->coef, ctx->fcoef, ctx->coef32);
+    k_coef<D><<<(m + 127) / 128, 128, 0, s>>>(m, ctx->omega, ctx->coef, ctx->fcoef, ctx->coef32);
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
 
-mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
+static mlpg_status init_operator_storage(mlpg_ctx *ctx) {
+    return ctx->dim == 3 ? init_operator_storage_d<3>(ctx) : init_operator_storage_d<2>(ctx);
+}
+
+template <int D>
+static mlpg_status form_operators_d(mlpg_ctx *ctx, double kappa) {
     const int64_t n = ctx->n, nnz = ctx->nnz;
     const int m = ctx->m;
     cudaStream_t s = ctx->stream;
     if (!ctx->A64) MLPG_TRY(init_operator_storage(ctx));
-    const double *Sf = ctx->mats + 13 * nnz;
-    k_form_arrays<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, kappa, ctx->rowidx, ctx->tau, ctx->mats,
+    const double *Sf = ctx->mats + mat_S<D>() * nnz;
+    k_form_arrays<D><<<(nnz + 255) / 256, 256, 0, s>>>(nnz, kappa, ctx->rowidx, ctx->tau, ctx->mats,
                                                     ctx->A64, ctx->A32, ctx->T64, ctx->S64);
     CU_LAUNCH(ctx);
     int64_t tot = nnz * m;
-    k_materialize<<<(tot + 255) / 256, 256, 0, s>>>(nnz, m, ctx->A64, Sf, ctx->coef, ctx->fcoef, ctx->L64);
+    k_materialize<D><<<(tot + 255) / 256, 256, 0, s>>>(nnz, m, ctx->A64, Sf, ctx->coef, ctx->fcoef, ctx->L64);
     CU_LAUNCH(ctx);
     CU(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
-    double4 pb = make_double4(ctx->psi_b[0], ctx->psi_b[1], ctx->psi_b[2], ctx->psi_b[3]);
+    Inflow pb;
+    for (int f = 0; f < 6; ++f) pb.v[f] = ctx->psi_b[f];
     int64_t nm = n * m;
-    k_diag_rhs<<<(nm + 255) / 256, 256, 0, s>>>(n, m, ctx->diag, nnz, ctx->A64, Sf, ctx->coef, ctx->fcoef,
+    k_diag_rhs<D><<<(nm + 255) / 256, 256, 0, s>>>(n, m, ctx->diag, nnz, ctx->A64, Sf, ctx->coef, ctx->fcoef,
                                                 ctx->tau, ctx->vecs, pb, ctx->dinv64, ctx->dinv32, ctx->r64,
                                                 ctx->d_flag);
     CU_LAUNCH(ctx);
@@ -846,7 +917,7 @@ mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
     // block-Jacobi inverses of every direction
     {
         dim3 grid((unsigned)ctx->nblk, (unsigned)((m + 7) / 8));
-        k_block_inv<<<grid, 256, 0, s>>>(ctx->nblk, m, ctx->rowptr, ctx->col, nnz, ctx->A64, Sf, ctx->coef,
+        k_block_inv<D><<<grid, 256, 0, s>>>(ctx->nblk, m, ctx->rowptr, ctx->col, nnz, ctx->A64, Sf, ctx->coef,
                                          ctx->fcoef, ctx->bmember, ctx->bof, ctx->Pinv, ctx->Pinv16, ctx->Pscale,
                                          ctx->d_flag);
         CU_LAUNCH(ctx);
@@ -858,6 +929,10 @@ mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
     for (int f = 0; f < 6; ++f) ctx->ops_psib[f] = ctx->psi_b[f];
     ctx->st.spmm_bytes = 0;
     return MLPG_OK;
+}
+
+mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
+    return ctx->dim == 3 ? form_operators_d<3>(ctx, kappa) : form_operators_d<2>(ctx, kappa);
 }
 
 // Device time of each batched L-apply: event pairs from a pool, harvested
@@ -885,7 +960,8 @@ mlpg_status apply_L64_res(mlpg_ctx *ctx, const double *X, const double *B, doubl
     return MLPG_OK;
 }
 
-mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
+template <int DIM>
+static mlpg_status apply_L32_res_d(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
     Team tm = pick_team(ctx->m);
     int64_t grid = team_grid(ctx->n, tm);
     cudaStream_t s = ctx->stream;
@@ -896,16 +972,16 @@ mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *
 #define SPMM32_ARGS ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->A32, ctx->coef32, X, B, Y
 #define SPMM32_CASE(D)                                                                         \
     case D:                                                                                    \
-        if (exact && small) k_spmm32<D, true, int32_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);      \
-        else if (small) k_spmm32<D, false, int32_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);         \
-        else k_spmm32<D, false, int64_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);                    \
+        if (exact && small) k_spmm32<D, true, int32_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS); \
+        else if (small) k_spmm32<D, false, int32_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);    \
+        else k_spmm32<D, false, int64_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);               \
         break;
     switch (tm.dpl) {
         SPMM32_CASE(1) SPMM32_CASE(2) SPMM32_CASE(3) SPMM32_CASE(4) SPMM32_CASE(5) SPMM32_CASE(6)
         SPMM32_CASE(7) SPMM32_CASE(8) SPMM32_CASE(9) SPMM32_CASE(10) SPMM32_CASE(11) SPMM32_CASE(12)
         default:
-            if (small) k_spmm32<16, false, int32_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);
-            else k_spmm32<16, false, int64_t><<<grid, 256, 0, s>>>(SPMM32_ARGS);
+            if (small) k_spmm32<16, false, int32_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);
+            else k_spmm32<16, false, int64_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);
             break;
     }
     CU_LAUNCH(ctx);
@@ -913,13 +989,13 @@ mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *
         int64_t gb = team_grid(ctx->nbrow, tm);
         float sign = B ? -1.0f : 1.0f;
 #define FACE_CASE(D) \
-    case D: k_faces32<D><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr, ctx->bcol, \
+    case D: k_faces32<D, DIM><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr, ctx->bcol, \
                                           ctx->bval32, ctx->coef32, X, sign, Y); break;
         switch (tm.dpl) {
             FACE_CASE(1) FACE_CASE(2) FACE_CASE(3) FACE_CASE(4) FACE_CASE(5) FACE_CASE(6) FACE_CASE(8)
-            case 7: k_faces32<8><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr,
+            case 7: k_faces32<8, DIM><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr,
                                                     ctx->bcol, ctx->bval32, ctx->coef32, X, sign, Y); break;
-            default: k_faces32<16><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr,
+            default: k_faces32<16, DIM><<<gb, 256, 0, s>>>(ctx->nbrow, ctx->m, tm.tm_log2, ctx->nb, ctx->brow, ctx->bptr,
                                                        ctx->bcol, ctx->bval32, ctx->coef32, X, sign, Y); break;
         }
 #undef FACE_CASE
@@ -931,37 +1007,59 @@ mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *
     return MLPG_OK;
 }
 
+mlpg_status apply_L32_res(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
+    return ctx->dim == 3 ? apply_L32_res_d<3>(ctx, X, B, Y) : apply_L32_res_d<2>(ctx, X, B, Y);
+}
+
 mlpg_status apply_L64(mlpg_ctx *ctx, const double *X, double *Y) { return apply_L64_res(ctx, X, nullptr, Y); }
 mlpg_status apply_L32(mlpg_ctx *ctx, const float *X, float *Y) { return apply_L32_res(ctx, X, nullptr, Y); }
 
-mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F) {
+template <int DIM>
+static mlpg_status rhs_T_d(mlpg_ctx *ctx, const double *Psi_prev, double *F) {
     Team tm = pick_team(ctx->m);
-    int64_t grid = team_grid(ctx->n, tm);
     cudaStream_t s = ctx->stream;
-    grid = rowteam_grid(ctx->n, tm);
-    DISPATCH_DPL(tm.dpl, k_rhs64, ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->T64,
-                 ctx->coef, Psi_prev, ctx->r64, F);
+    const int64_t grid = rowteam_grid(ctx->n, tm);
+#define RHS_ARGS ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->T64, ctx->coef, Psi_prev, ctx->r64, F
+    switch (tm.dpl) {
+        case 1: k_rhs64<1, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+        case 2: k_rhs64<2, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+        case 3: k_rhs64<3, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+        case 4: k_rhs64<4, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+        case 5: case 6: k_rhs64<6, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+        case 7: case 8: k_rhs64<8, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+        default: k_rhs64<16, DIM><<<grid, 256, 0, s>>>(RHS_ARGS); break;
+    }
+#undef RHS_ARGS
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status rhs_T(mlpg_ctx *ctx, const double *Psi_prev, double *F) {
+    return ctx->dim == 3 ? rhs_T_d<3>(ctx, Psi_prev, F) : rhs_T_d<2>(ctx, Psi_prev, F);
+}
+
+template <typename T, int D>
+static mlpg_status apply_MS_d(mlpg_ctx *ctx, const double *phi, T *out) {
+    const int64_t n = ctx->n;
+    cudaStream_t s = ctx->stream;
+    k_ms_spmv<D><<<(n + 255) / 256, 256, 0, s>>>(n, ctx->nnz, ctx->rowptr, ctx->col, ctx->S64, phi, ctx->abc);
+    CU_LAUNCH(ctx);
+    int64_t nm = n * ctx->m;
+    if constexpr (sizeof(T) == 4) {
+        float *abc32 = (float *)(ctx->abc + NT<D>() * n);
+        k_abc32<<<(NT<D>() * n + 255) / 256, 256, 0, s>>>(NT<D>() * n, ctx->abc, abc32);
+        CU_LAUNCH(ctx);
+        k_ms_expand32<D><<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, abc32, ctx->coef32, (float *)out);
+    } else {
+        k_ms_expand<T, D><<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, ctx->abc, ctx->coef, out);
+    }
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
 
 template <typename T>
 mlpg_status apply_MS(mlpg_ctx *ctx, const double *phi, T *out) {
-    const int64_t n = ctx->n;
-    cudaStream_t s = ctx->stream;
-    k_ms_spmv<<<(n + 255) / 256, 256, 0, s>>>(n, ctx->nnz, ctx->rowptr, ctx->col, ctx->S64, phi, ctx->abc);
-    CU_LAUNCH(ctx);
-    int64_t nm = n * ctx->m;
-    if constexpr (sizeof(T) == 4) {
-        float *abc32 = (float *)(ctx->abc + 3 * n);
-        k_abc32<<<(3 * n + 255) / 256, 256, 0, s>>>(n, ctx->abc, abc32);
-        CU_LAUNCH(ctx);
-        k_ms_expand32<<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, abc32, ctx->coef32, (float *)out);
-    } else {
-        k_ms_expand<T><<<(nm + 255) / 256, 256, 0, s>>>(n, ctx->m, ctx->abc, ctx->coef, out);
-    }
-    CU_LAUNCH(ctx);
-    return MLPG_OK;
+    return ctx->dim == 3 ? apply_MS_d<T, 3>(ctx, phi, out) : apply_MS_d<T, 2>(ctx, phi, out);
 }
 template mlpg_status apply_MS<double>(mlpg_ctx *, const double *, double *);
 template mlpg_status apply_MS<float>(mlpg_ctx *, const double *, float *);

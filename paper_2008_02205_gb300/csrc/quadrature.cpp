@@ -80,4 +80,25 @@ void triangle_rule(int n1d, double *xi, double *w) {
     }
 }
 
+// Reference tetrahedron: collapsed coordinates u (Gauss-Jacobi(2,0)),
+// v (Gauss-Jacobi(1,0)), r (Gauss-Legendre) on [0, 1]; xi = (u, v(1-u),
+// r(1-u)(1-v)); the Jacobi weights carry the Jacobian (1-u)^2 (1-v).  Exact for
+// total degree 2 n1d - 1 (n1d = 2: the paper's 3D order 3 with 8 points).
+void tet_rule(int n1d, double *xi, double *w) {
+    double tu[64], wu[64], tv[64], wv[64], tr[64], wr[64];
+    gauss_jacobi_newton(n1d, 2.0, 0.0, tu, wu);
+    gauss_jacobi_newton(n1d, 1.0, 0.0, tv, wv);
+    gauss_jacobi_newton(n1d, 0.0, 0.0, tr, wr);
+    int k = 0;
+    for (int i = 0; i < n1d; ++i)
+        for (int j = 0; j < n1d; ++j)
+            for (int l = 0; l < n1d; ++l, ++k) {
+                double u = 0.5 * (1.0 + tu[i]), v = 0.5 * (1.0 + tv[j]), r = 0.5 * (1.0 + tr[l]);
+                xi[3 * k] = u;
+                xi[3 * k + 1] = v * (1.0 - u);
+                xi[3 * k + 2] = r * (1.0 - u) * (1.0 - v);
+                w[k] = wu[i] * wv[j] * wr[l] / 64.0;
+            }
+}
+
 }  // namespace mlpg
