@@ -255,17 +255,25 @@ def two_region_2d(n_per_dim: int = 256, sn: int = 8, seed: int = 2000, steps: in
 
 
 def lognormal_3d(n_per_dim: int = 40, sn: int = 8, seed: int = 3000, steps: int = 10,
-                 dt: float = 0.01):
+                 dt: float = 0.01, refine=None):
     """3D unit cube, jittered lattice, S_sn, sigma_t ~ lognormal(0, 1) per point,
     sigma_s = 0.8 sigma_t, no volume source, isotropic inflow psi_b = 1 on the
-    x = 0 face.  Defaults: 40^3 points, S8 (80 directions), 10 steps of 0.01."""
+    x = 0 face.  Defaults: 40^3 points, S8 (80 directions), 10 steps of 0.01.
+    refine = (min_level, goal_level, cone_deg) replaces S_sn by the selectively
+    refined hierarchical quadrature of Alg. 2 around +x (the configuration's
+    refinement within 15 degrees of +x: (1, 5, 15.0), 272 directions)."""
     def st(x, rng):
         return rng.lognormal(0.0, 1.0, size=x.shape[0])
 
     def ss(x, rng, sig_t):
         return 0.8 * sig_t
-    return make_problem(f"3d-lognormal-{n_per_dim}^3-S{sn}", n_per_dim, 3, sn, seed,
-                        st, ss, 0.0, dt, steps, inflow={0: 1.0})
+    p = make_problem(f"3d-lognormal-{n_per_dim}^3-S{sn}", n_per_dim, 3, sn, seed,
+                     st, ss, 0.0, dt, steps, inflow={0: 1.0})
+    if refine is not None:
+        lo, goal, cone = refine
+        p.omega, p.w = refined_quadrature(lo, goal, cone_hits((1.0, 0.0, 0.0), cone))
+        p.name = f"3d-lognormal-{n_per_dim}^3-refined{lo}-{goal}-{cone:g}deg"
+    return p
 
 
 def batched_2d(count: int = 64, seed: int = 4000, n_range=(1024, 65536),
@@ -287,3 +295,66 @@ def batched_2d(count: int = 64, seed: int = 4000, n_range=(1024, 65536),
         out.append(make_problem(f"2d-batch{b}-{k}x{k}-S{sn}", k, 2, sn, seed + b,
                                 sig_t, ratio * sig_t, 1.0, dt, steps))
     return out
+
+
+# ---------------------------------------------------------------------------
+# hierarchical octant quadrature and selective refinement (Sec. 4.3, Alg. 2)
+# ---------------------------------------------------------------------------
+def _octant_triangles(level: int):
+    """Spherical triangles of the unit sphere at a refinement level: the eight
+    octants, each split `level` times into four by its normalised edge
+    midpoints.  Children of triangle t are 4t .. 4t + 3, so the level-G
+    descendants of a level-l triangle t are t 4^(G-l) .. (t + 1) 4^(G-l) - 1."""
+    tris = []
+    for sx in (1.0, -1.0):
+        for sy in (1.0, -1.0):
+            for sz in (1.0, -1.0):
+                tris.append((np.array([sx, 0, 0]), np.array([0, sy, 0]), np.array([0, 0, sz])))
+    for _ in range(level):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (v / np.linalg.norm(v) for v in (a + b, b + c, c + a))
+            nxt += [(a, ab, ca), (ab, b, bc), (ca, bc, c), (ab, bc, ca)]
+        tris = nxt
+    return tris
+
+
+def _tri_ordinates(tris):
+    """Ordinate (normalised vertex centroid) and weight (spherical area, by the
+    Van Oosterom-Strackee formula) of each spherical triangle."""
+    om = np.array([(a + b + c) / np.linalg.norm(a + b + c) for a, b, c in tris])
+    w = np.array([2.0 * np.arctan2(abs(a @ np.cross(b, c)), 1.0 + a @ b + b @ c + c @ a) for a, b, c in tris])
+    return om, w
+
+
+def refined_quadrature(min_level: int, goal_level: int, hits):
+    """Selective refinement of the hierarchical octant quadrature (Alg. 2):
+    start from the goal level; for each coarser level from min_level up, an
+    ordinate whose goal-level descendants all miss the object (hits(omega)
+    False for each) and are all still unmerged replaces them; the goal
+    ordinates left are kept.  Weights are exact spherical areas, so they sum
+    to 4 pi.  Returns (omega[M, 3], w[M])."""
+    G = goal_level
+    gom, gw = _tri_ordinates(_octant_triangles(G))
+    hit = np.array([bool(hits(o)) for o in gom])
+    present = np.ones(len(gom), bool)
+    om_out, w_out = [], []
+    for lev in range(min_level, G):
+        lom, lw = _tri_ordinates(_octant_triangles(lev))
+        span = 4 ** (G - lev)
+        for t in range(len(lom)):
+            d = slice(t * span, (t + 1) * span)
+            if present[d].all() and not hit[d].any():
+                om_out.append(lom[t])
+                w_out.append(lw[t])
+                present[d] = False
+    om_out += list(gom[present])
+    w_out += list(gw[present])
+    return np.array(om_out), np.array(w_out)
+
+
+def cone_hits(axis=(1.0, 0.0, 0.0), half_angle_deg: float = 15.0):
+    """Directions within half_angle_deg of axis."""
+    ax = np.asarray(axis, float) / np.linalg.norm(axis)
+    c = np.cos(np.radians(half_angle_deg))
+    return lambda o: float(np.asarray(o) @ ax) >= c
