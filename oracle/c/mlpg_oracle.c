@@ -33,8 +33,9 @@
  *   - 3D cells are fanned into tetrahedra (x_i, c_f, f_k, f_{k+1}), one per edge
  *     of every face f, c_f the average of f's vertices; boundary faces into
  *     triangles (c_f, f_k, f_{k+1}).
- *   - RK basis P_j(x) = [1, (x - x_j)/s] with s = h of the point owning the
- *     evaluation point (any common scale gives the same U in exact arithmetic).
+ *   - RK basis P_j(x): the monomials of (x - x_j)/s up to the RK order (linear:
+ *     [1, (x - x_j)/s]) with s = h of the point owning the evaluation point (any
+ *     common scale gives the same U in exact arithmetic).
  */
 #include <math.h>
 #include <stdint.h>
@@ -752,21 +753,45 @@ static int dense_solve(int n, double *A, double *b)
     return 0;
 }
 
+/* Basis of the RK correction (Sec. 2.2): all monomials of xi = (x - x_j)/s up
+ * to total degree `order` (0, 1 or 2), ordered 1, xi_a, xi_a xi_b (a <= b).
+ * P[np] and its derivatives dP[g][np] = d P / d xi_g.  Returns np. */
+static int rk_basis(int dim, int order, const double *xi, double *P, double dP[3][10])
+{
+    int k = 0;
+    P[k] = 1.0;
+    for (int g = 0; g < dim; ++g) dP[g][k] = 0.0;
+    ++k;
+    if (order >= 1)
+        for (int a = 0; a < dim; ++a, ++k) {
+            P[k] = xi[a];
+            for (int g = 0; g < dim; ++g) dP[g][k] = (g == a) ? 1.0 : 0.0;
+        }
+    if (order >= 2)
+        for (int a = 0; a < dim; ++a)
+            for (int b = a; b < dim; ++b, ++k) {
+                P[k] = xi[a] * xi[b];
+                for (int g = 0; g < dim; ++g) dP[g][k] = (g == a ? xi[b] : 0.0) + (g == b ? xi[a] : 0.0);
+            }
+    return k;
+}
+
 /* RK functions at the point xe from the candidate list cand[ncand].
  * Supported j: |xe - x_j| < R_j.  Writes idx[ns], U[ns], dU[ns*dim]; returns
  * ns, or ORC_ERR_SINGULAR if the moment matrix cannot be inverted.
  *   M = sum_j V_j W_j P_j P_j^T,   C = M^{-1} e_1
  *   d_g M = sum_j V_j [(d_g P_j P_j^T + P_j d_g P_j^T) W_j + P_j P_j^T d_g W_j]
  *   d_g C = -M^{-1} (d_g M) C
- *   U_j = W_j P_j^T C,  d_g U_j = W_j (d_g P_j^T C + P_j^T d_g C) + P_j^T C d_g W_j */
-static int rk_eval(int dim, const double *xe, double s, int ncand, const int32_t *cand,
+ *   U_j = W_j P_j^T C,  d_g U_j = W_j (d_g P_j^T C + P_j^T d_g C) + P_j^T C d_g W_j
+ * with d_g P = (d P / d xi_g) / s. */
+static int rk_eval(int dim, int order, const double *xe, double s, int ncand, const int32_t *cand,
                    const double *x, const double *R, const double *V, int32_t *idx, double *U,
                    double *dU)
 {
-    const int np = dim + 1;
-    double M[16] = {0}, dM[3][16] = {{0}};
-    int ns = 0;
-    double W[1024], dW[1024][3], P[1024][4];
+    static double W[1024], dW[1024][3], P[1024][10], dPa[1024][3][10];
+    double M[100] = {0}, dM[3][100] = {{0}};
+    int ns = 0, np = 1;
+    if (order < 0 || order > 2) return ORC_ERR_ARG;
     for (int c = 0; c < ncand; ++c) {
         int32_t j = cand[c];
         double d[3] = {0, 0, 0}, r2 = 0.0;
@@ -780,29 +805,28 @@ static int rk_eval(int dim, const double *xe, double s, int ncand, const int32_t
         W[ns] = kernel_w(chi);
         double g = (r > 0.0) ? kernel_dw(chi) / (r * h) : 0.0;
         for (int k = 0; k < dim; ++k) dW[ns][k] = g * d[k];
-        P[ns][0] = 1.0;
-        for (int k = 0; k < dim; ++k) P[ns][k + 1] = d[k] / s;
+        double xi[3] = {d[0] / s, d[1] / s, d[2] / s};
+        np = rk_basis(dim, order, xi, P[ns], dPa[ns]);
+        for (int gg = 0; gg < dim; ++gg)
+            for (int k = 0; k < np; ++k) dPa[ns][gg][k] /= s;   /* d/dx = (d/dxi) / s */
         ++ns;
     }
+    if (ns == 0) return ORC_ERR_SINGULAR;
     for (int a = 0; a < ns; ++a) {
         double v = V[idx[a]];
         for (int r = 0; r < np; ++r)
             for (int c = 0; c < np; ++c) {
                 M[r * np + c] += v * W[a] * P[a][r] * P[a][c];
-                for (int g = 0; g < dim; ++g) {
-                    /* d_g P has a single entry 1/s at position g + 1 */
-                    double dPr = (r == g + 1) ? 1.0 / s : 0.0;
-                    double dPc = (c == g + 1) ? 1.0 / s : 0.0;
-                    dM[g][r * np + c] += v * ((dPr * P[a][c] + P[a][r] * dPc) * W[a] +
+                for (int g = 0; g < dim; ++g)
+                    dM[g][r * np + c] += v * ((dPa[a][g][r] * P[a][c] + P[a][r] * dPa[a][g][c]) * W[a] +
                                               P[a][r] * P[a][c] * dW[a][g]);
-                }
             }
     }
-    double A[16], C[4];
+    double A[100], C[10];
     memcpy(A, M, sizeof(A));
     for (int r = 0; r < np; ++r) C[r] = (r == 0) ? 1.0 : 0.0;
     if (dense_solve(np, A, C)) return ORC_ERR_SINGULAR;
-    double dC[3][4];
+    double dC[3][10];
     for (int g = 0; g < dim; ++g) {
         for (int r = 0; r < np; ++r) {
             double t = 0.0;
@@ -817,9 +841,11 @@ static int rk_eval(int dim, const double *xe, double s, int ncand, const int32_t
         for (int r = 0; r < np; ++r) PC += P[a][r] * C[r];
         U[a] = W[a] * PC;
         for (int g = 0; g < dim; ++g) {
-            double dPC = C[g + 1] / s; /* d_g P^T C */
-            double PdC = 0.0;
-            for (int r = 0; r < np; ++r) PdC += P[a][r] * dC[g][r];
+            double dPC = 0.0, PdC = 0.0;
+            for (int r = 0; r < np; ++r) {
+                dPC += dPa[a][g][r] * C[r];
+                PdC += P[a][r] * dC[g][r];
+            }
             dU[a * dim + g] = W[a] * (dPC + PdC) + PC * dW[a][g];
         }
     }
@@ -830,7 +856,7 @@ static int rk_eval(int dim, const double *xe, double s, int ncand, const int32_t
  * owner[p] and the basis scale is h_owner = R_owner / 2.  CSR output: sptr[npts+1],
  * sidx, U, dU[*dim].  Pass sidx == NULL to count only.  Returns total entries or
  * a negative error. */
-int64_t orc_rk_at_points(int dim, int64_t n, const double *x, const double *R, const double *V,
+int64_t orc_rk_at_points(int dim, int order, int64_t n, const double *x, const double *R, const double *V,
                          const int64_t *rowptr, const int32_t *col, int64_t npts,
                          const double *pts, const int32_t *owner, int64_t *sptr, int32_t *sidx,
                          double *U, double *dU)
@@ -840,7 +866,7 @@ int64_t orc_rk_at_points(int dim, int64_t n, const double *x, const double *R, c
     sptr[0] = 0;
     for (int64_t p = 0; p < npts; ++p) {
         int32_t o = owner[p];
-        int ns = rk_eval(dim, pts + p * dim, 0.5 * R[o], (int)(rowptr[o + 1] - rowptr[o]),
+        int ns = rk_eval(dim, order, pts + p * dim, 0.5 * R[o], (int)(rowptr[o + 1] - rowptr[o]),
                          col + rowptr[o], x, R, V, idx, u, du);
         if (ns < 0) return ns;
         if (sidx) {
@@ -884,7 +910,7 @@ static int64_t find_pos(const int64_t *rowptr, const int32_t *col, int32_t a, in
 int orc_n_mats(int dim) { return 3 + 3 * dim + dim * dim + 2 * dim; }
 int orc_n_vecs(int dim) { return 1 + dim + 2 * dim; }
 
-int orc_assemble(int dim, int64_t n, const double *x, const double *R, const double *V,
+int orc_assemble(int dim, int order, int64_t n, const double *x, const double *R, const double *V,
                  const int64_t *rowptr, const int32_t *col, int64_t nvq, const double *xq,
                  const double *wq, const int32_t *qowner, const double *sig_t_q,
                  const double *sig_s_q, const double *q_q, int64_t nbq, const double *xb,
@@ -904,7 +930,7 @@ int orc_assemble(int dim, int64_t n, const double *x, const double *R, const dou
     double U[1024], dU[3 * 1024];
     for (int64_t p = 0; p < nvq; ++p) {
         int32_t o = qowner[p];
-        int ns = rk_eval(dim, xq + p * dim, 0.5 * R[o], (int)(rowptr[o + 1] - rowptr[o]),
+        int ns = rk_eval(dim, order, xq + p * dim, 0.5 * R[o], (int)(rowptr[o + 1] - rowptr[o]),
                          col + rowptr[o], x, R, V, idx, U, dU);
         if (ns < 0) return ns;
         double w = wq[p], st = sig_t_q[p], ss = sig_s_q[p], qv = q_q[p];
@@ -933,7 +959,7 @@ int orc_assemble(int dim, int64_t n, const double *x, const double *R, const dou
     }
     for (int64_t p = 0; p < nbq; ++p) {
         int32_t o = bowner[p];
-        int ns = rk_eval(dim, xb + p * dim, 0.5 * R[o], (int)(rowptr[o + 1] - rowptr[o]),
+        int ns = rk_eval(dim, order, xb + p * dim, 0.5 * R[o], (int)(rowptr[o + 1] - rowptr[o]),
                          col + rowptr[o], x, R, V, idx, U, dU);
         if (ns < 0) return ns;
         int f = bface[p];

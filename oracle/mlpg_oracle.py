@@ -77,7 +77,7 @@ def lib():
         L.orc_volume_qps_2d.restype = i64
         L.orc_boundary_qps_2d.argtypes = [i64, P, P, P, i32, P, P, P, P]
         L.orc_boundary_qps_2d.restype = i64
-        L.orc_rk_at_points.argtypes = [i32, i64, P, P, P, P, P, i64, P, P, P, P, P, P]
+        L.orc_rk_at_points.argtypes = [i32, i32, i64, P, P, P, P, P, i64, P, P, P, P, P, P]
         L.orc_rk_at_points.restype = i64
         L.orc_n_mats.argtypes = [i32]
         L.orc_n_vecs.argtypes = [i32]
@@ -88,7 +88,7 @@ def lib():
         L.orc_volume_qps_3d.restype = i64
         L.orc_boundary_qps_3d.argtypes = [i64, P, P, P, P, i32, P, P, P, P]
         L.orc_boundary_qps_3d.restype = i64
-        L.orc_assemble.argtypes = [i32, i64, P, P, P, P, P, i64, P, P, P, P, P, P, i64, P, P, P, P, P, P]
+        L.orc_assemble.argtypes = [i32, i32, i64, P, P, P, P, P, i64, P, P, P, P, P, P, i64, P, P, P, P, P, P]
         L.orc_assemble.restype = i32
         _lib = L
     return _lib
@@ -233,7 +233,7 @@ def boundary_qps_3d(n, fptr, vptr, verts, labels, nref=2):
     return QP(xb, wb, ow, fc)
 
 
-def rk_at_points(x, R, V, rowptr, col, pts, owner):
+def rk_at_points(x, R, V, rowptr, col, pts, owner, order=1):
     """RK functions U_j and gradients at arbitrary points (Sec. 2.2).
 
     Candidates for point p: the overlap row of owner[p].  Returns (sptr, sidx,
@@ -245,14 +245,14 @@ def rk_at_points(x, R, V, rowptr, col, pts, owner):
     npts = pts.shape[0]
     sptr = np.zeros(npts + 1, np.int64)
     L = lib()
-    tot = L.orc_rk_at_points(dim, n, _p(x), _p(R), _p(V), _p(rowptr), _p(col), npts, _p(pts), _p(owner),
+    tot = L.orc_rk_at_points(dim, order, n, _p(x), _p(R), _p(V), _p(rowptr), _p(col), npts, _p(pts), _p(owner),
                              _p(sptr), None, None, None)
     if tot < 0:
         raise FloatingPointError(f"RK moment matrix singular (code {tot})")
     sidx = np.zeros(tot, np.int32)
     U = np.zeros(tot)
     dU = np.zeros((tot, dim))
-    L.orc_rk_at_points(dim, n, _p(x), _p(R), _p(V), _p(rowptr), _p(col), npts, _p(pts), _p(owner),
+    L.orc_rk_at_points(dim, order, n, _p(x), _p(R), _p(V), _p(rowptr), _p(col), npts, _p(pts), _p(owner),
                        _p(sptr), _p(sidx), _p(U), _p(dU))
     return sptr, sidx, U, dU
 
@@ -271,7 +271,7 @@ class Discretization:
     quadrature points and the integrated forms of Sec. 4.1."""
 
     def __init__(self, x, R, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), nref_tri=5, nref_line=5,
-                 nref_tet=2, nref_face=2):
+                 nref_tet=2, nref_face=2, rk_order=1):
         """2D: 5x5 conical-product triangles (degree 9) and 5-point Gauss-Legendre
         edges.  3D: 2x2x2 conical-product tetrahedra and 2x2 boundary triangles,
         degree 3 like the paper's 8-point third-order rule (Sec. 5)."""
@@ -283,6 +283,7 @@ class Discretization:
         self.lo = np.asarray(lo, np.float64)
         self.hi = np.asarray(hi, np.float64)
         self.h = 0.5 * self.R                       # smoothing length
+        self.rk_order = int(rk_order)               # RK correction order 0, 1 or 2 (Sec. 2.2)
         self.rowptr, self.col = neighbors(self.x, self.R)
         if self.dim == 2:
             self.cptr, self.verts, self.labels, self.V = cells_2d(
@@ -305,7 +306,7 @@ class Discretization:
         mats = np.zeros((nm, nnz))
         vecs = np.zeros((nv, n))
         st, ss, qq = (_c(a, np.float64) for a in (sigma_t_q, sigma_s_q, q_q))
-        rc = L.orc_assemble(d, n, _p(self.x), _p(self.R), _p(self.V), _p(self.rowptr), _p(self.col),
+        rc = L.orc_assemble(d, self.rk_order, n, _p(self.x), _p(self.R), _p(self.V), _p(self.rowptr), _p(self.col),
                                len(self.vq.w), _p(self.vq.x), _p(self.vq.w), _p(self.vq.owner),
                                _p(st), _p(ss), _p(qq),
                                len(self.bq.w), _p(self.bq.x), _p(self.bq.w), _p(self.bq.face), _p(self.bq.owner),
@@ -337,7 +338,7 @@ class Discretization:
     def interpolation_matrix(self):
         """phi_i = sum_j V_j U_j(x_i) Phi_j  (Eq. flux-expansion at the centres)."""
         sptr, sidx, U, _ = rk_at_points(self.x, self.R, self.V, self.rowptr, self.col, self.x,
-                                        np.arange(self.n, dtype=np.int32))
+                                        np.arange(self.n, dtype=np.int32), self.rk_order)
         return sp.csr_matrix((U * self.V[sidx], sidx, sptr), shape=(self.n, self.n))
 
 
