@@ -70,6 +70,10 @@ typedef struct {
     int mixed_half_prec;   /* MLPG_MIXED: 1 = the FP32 correction solves use the block-Jacobi
                               inverses stored in FP16 (scaled by a power of two per block and
                               direction), 0 = FP32 inverses; default 1 */
+    int rk_order;          /* order of the RK correction (Sec. 2.2): 0 (constants reproduced),
+                              1 (linear) or 2 (quadratic; needs kernels spanning at least five
+                              neighbours, e.g. extent 2.5-3 point spacings); 3D: 1 only;
+                              default 1 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
 } mlpg_options;
 

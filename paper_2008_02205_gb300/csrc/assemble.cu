@@ -202,6 +202,137 @@ __device__ uint64_t rk_point_tab(double px, double py, double s, int S, const do
     return mask;
 }
 
+// RK functions of order ORD (0 or 2; order 1 is rk_point_tab) at (px, py):
+// the basis is every monomial of xi = (p - x_j)/s up to degree ORD, ordered
+// 1, xi_x, xi_y, xi_x^2, xi_x xi_y, xi_y^2.  Same table layout, first-pass use
+// of the table and return value (support mask, 0 when the moment matrix is
+// not positive definite) as rk_point_tab.
+template <int ORD>
+__device__ uint64_t rk_point_gen(double px, double py, double s, int S, const double *fx, const double *fy,
+                                 const double *fR2, const double *finvh, const double *fV, double *U, double *Ux,
+                                 double *Uy, int stride) {
+    constexpr int NP = ORD == 0 ? 1 : (ORD == 1 ? 3 : 6);
+    double M[NP][NP], Dx[NP][NP], Dy[NP][NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) M[i][j] = Dx[i][j] = Dy[i][j] = 0.0;
+    const double is = 1.0 / s;
+    // basis and its x, y derivatives at offset (dx, dy)
+    auto basis = [&](double dx, double dy, double *P, double *Px, double *Py) {
+        const double ex = dx * is, ey = dy * is;
+        P[0] = 1.0; Px[0] = 0.0; Py[0] = 0.0;
+        if (ORD >= 1) {
+            P[1] = ex; Px[1] = is; Py[1] = 0.0;
+            P[2] = ey; Px[2] = 0.0; Py[2] = is;
+        }
+        if (ORD >= 2) {
+            P[3] = ex * ex; Px[3] = 2.0 * ex * is; Py[3] = 0.0;
+            P[4] = ex * ey; Px[4] = ey * is; Py[4] = ex * is;
+            P[5] = ey * ey; Px[5] = 0.0; Py[5] = 2.0 * ey * is;
+        }
+    };
+    uint64_t mask = 0;
+    for (int a = 0; a < S; ++a) {
+        const double dx = px - fx[a], dy = py - fy[a];
+        const double r2 = dx * dx + dy * dy;
+        if (!(r2 < fR2[a])) {
+            U[a * stride] = 0.0;
+            Ux[a * stride] = 0.0;
+            Uy[a * stride] = 0.0;
+            continue;
+        }
+        mask |= uint64_t(1) << a;
+        const double ir = r2 > 0.0 ? rsqrt(r2) : 0.0;
+        const double chi = r2 * ir * finvh[a];
+        const double W = spline_w(chi), g = spline_dw(chi) * finvh[a] * ir;
+        const double Wx = g * dx, Wy = g * dy, v = fV[a];
+        U[a * stride] = W;
+        Ux[a * stride] = Wx;
+        Uy[a * stride] = Wy;
+        double P[NP], Px[NP], Py[NP];
+        basis(dx, dy, P, Px, Py);
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const double pp = P[i] * P[j];
+                M[i][j] += v * W * pp;
+                Dx[i][j] += v * ((Px[i] * P[j] + P[i] * Px[j]) * W + pp * Wx);
+                Dy[i][j] += v * ((Py[i] * P[j] + P[i] * Py[j]) * W + pp * Wy);
+            }
+    }
+    // Cholesky M = L L^T
+    double L[NP][NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        double d = M[j][j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 1e-14 * M[j][j])) return 0;
+        L[j][j] = sqrt(d);
+#pragma unroll
+        for (int i = j + 1; i < NP; ++i) {
+            double t = M[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
+            L[i][j] = t / L[j][j];
+        }
+    }
+    auto solve = [&](double *b) {   // in place: b <- M^{-1} b
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            double t = b[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) t -= L[i][k] * b[k];
+            b[i] = t / L[i][i];
+        }
+#pragma unroll
+        for (int i = NP - 1; i >= 0; --i) {
+            double t = b[i];
+#pragma unroll
+            for (int k = i + 1; k < NP; ++k) t -= L[k][i] * b[k];
+            b[i] = t / L[i][i];
+        }
+    };
+    double C[NP], Cx[NP], Cy[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) C[i] = i == 0 ? 1.0 : 0.0;
+    solve(C);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        double tx = 0.0, ty = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            tx += Dx[i][j] * C[j];
+            ty += Dy[i][j] * C[j];
+        }
+        Cx[i] = -tx;
+        Cy[i] = -ty;
+    }
+    solve(Cx);
+    solve(Cy);
+    for (uint64_t bits = mask; bits; bits &= bits - 1) {
+        const int a = __ffsll((long long)bits) - 1;
+        const double W = U[a * stride], Wx = Ux[a * stride], Wy = Uy[a * stride];
+        double P[NP], Px[NP], Py[NP];
+        basis(px - fx[a], py - fy[a], P, Px, Py);
+        double PC = 0.0, dxC = 0.0, dyC = 0.0, PCx = 0.0, PCy = 0.0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            PC += P[i] * C[i];
+            dxC += Px[i] * C[i];
+            dyC += Py[i] * C[i];
+            PCx += P[i] * Cx[i];
+            PCy += P[i] * Cy[i];
+        }
+        U[a * stride] = W * PC;
+        Ux[a * stride] = W * (dxC + PCx) + PC * Wx;
+        Uy[a * stride] = W * (dyC + PCy) + PC * Wy;
+    }
+    return mask;
+}
+
 __device__ int find_col(const int32_t *__restrict__ col, int32_t lo, int32_t hi, int32_t key) {
     hi -= 1;
     while (lo <= hi) {
@@ -224,7 +355,13 @@ struct AsmArgs {
 };
 
 // mats layout: 0 M0, 1 Mt, 2 Ms, 3-4 G, 5-6 Gt, 7-8 Gs, 9-12 K (xx, xy, yx, yy), 13-16 S_f
+// ORD: RK order; MAXS: functions reaching one cell (<= 64, one mask word);
+// CHUNK: quadrature points per RK pass.  The linear path is <1, 40, 64>.
+template <int ORD, int MAXS, int CHUNK>
 __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
+    constexpr int kMaxS = MAXS, kChunk = CHUNK, kPairs = MAXS * MAXS;
+    constexpr int kPPT = (kPairs + kThreads - 1) / kThreads;
+    static_assert(MAXS <= 64 && CHUNK <= kThreads, "one 64-bit support mask per point");
     const int64_t i = blockIdx.x;
     __shared__ double fx[kMaxS], fy[kMaxS], fR[kMaxS], fV[kMaxS], fR2[kMaxS], finvh[kMaxS];
     __shared__ uint64_t tMask[kChunk];
@@ -328,7 +465,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
                 int f = -A.labels[c0 + e] - 1;
                 fslot = (f == face_slot[0]) ? 0 : 1;
             }
-            uint64_t mk = rk_point_tab(px, py, scale, nS, fx, fy, fR2, finvh, fV, tU + tid, tUx + tid, tUy + tid,
+            uint64_t mk;
+            if constexpr (ORD == 1)
+                mk = rk_point_tab(px, py, scale, nS, fx, fy, fR2, finvh, fV, tU + tid, tUx + tid, tUy + tid, kChunk);
+            else
+                mk = rk_point_gen<ORD>(px, py, scale, nS, fx, fy, fR2, finvh, fV, tU + tid, tUx + tid, tUy + tid,
                                        kChunk);
             if (!mk) atomicOr(A.flag, 1);
             tMask[tid] = mk;
@@ -429,6 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
 }
 
 // RK point interpolation at the centres: interp[pos(i, j)] = V_j U_j(x_i).
+template <int ORD>
 __global__ void k_interp_2d(int64_t n, const double *__restrict__ x, const double *__restrict__ R,
                             const double *__restrict__ V, const int32_t *__restrict__ rowptr,
                             const int32_t *__restrict__ col, double *__restrict__ interp,
@@ -452,7 +594,18 @@ __global__ void k_interp_2d(int64_t n, const double *__restrict__ x, const doubl
     }
     if (S > 2 * kMaxS) { atomicOr(flag, 2); return; }
     double U[kMaxS * 2], Ux[kMaxS * 2], Uy[kMaxS * 2];
-    if (!rk_point(px, py, 0.5 * R[i], S, fx, fy, fR, fV, U, Ux, Uy, 1)) {
+    bool ok;
+    if constexpr (ORD == 1) {
+        ok = rk_point(px, py, 0.5 * R[i], S, fx, fy, fR, fV, U, Ux, Uy, 1);
+    } else {
+        double fR2[kMaxS * 2], finvh[kMaxS * 2];
+        for (int a = 0; a < S; ++a) {
+            fR2[a] = fR[a] * fR[a];
+            finvh[a] = 2.0 / fR[a];
+        }
+        ok = S <= 64 && rk_point_gen<ORD>(px, py, 0.5 * R[i], S, fx, fy, fR2, finvh, fV, U, Ux, Uy, 1) != 0;
+    }
+    if (!ok) {
         atomicOr(flag, 1);
         return;
     }
@@ -493,8 +646,14 @@ mlpg_status run_interp(mlpg_ctx *ctx) {
     CU(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
     CU(ctx, cudaMemsetAsync(ctx->interp, 0, ctx->nnz * sizeof(double), ctx->stream));
     int B = 128;
-    k_interp_2d<<<(ctx->n + B - 1) / B, B, 0, ctx->stream>>>(ctx->n, ctx->x, ctx->R, ctx->V, ctx->rowptr,
-                                                            ctx->col, ctx->interp, ctx->d_flag);
+    const int ord = ctx->opt.rk_order;
+    auto launch = [&](auto kern) {
+        kern<<<(ctx->n + B - 1) / B, B, 0, ctx->stream>>>(ctx->n, ctx->x, ctx->R, ctx->V, ctx->rowptr, ctx->col,
+                                                          ctx->interp, ctx->d_flag);
+    };
+    if (ord == 0) launch(k_interp_2d<0>);
+    else if (ord == 2) launch(k_interp_2d<2>);
+    else launch(k_interp_2d<1>);
     CU_LAUNCH(ctx);
     return check_flag(ctx, "interpolation");
 }
@@ -516,10 +675,17 @@ mlpg_status run_assemble(mlpg_ctx *ctx) {
     a.verts = ctx->verts;
     a.ntri = tri1d * tri1d; a.nline = nline;
     a.mats = ctx->mats; a.vecs = ctx->vecs; a.flag = ctx->d_flag;
-    size_t smem = sizeof(double) * (3 * kChunk * kMaxS + kChunk + kChunk / 2 + 1 + 9 * kPairs);
-    CU(ctx, cudaFuncSetAttribute(k_assemble_2d, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_assemble_2d<<<ctx->n, kThreads, smem, ctx->stream>>>(a);
-    CU_LAUNCH(ctx);
+    // shared table + weights + faces + pair sums for <ORD, MAXS, CHUNK>
+    auto run = [&](auto kern, int maxs, int chunk) -> mlpg_status {
+        size_t smem = sizeof(double) * (3 * (size_t)chunk * maxs + chunk + chunk / 2 + 1 + 9 * (size_t)maxs * maxs);
+        CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kern<<<ctx->n, kThreads, smem, ctx->stream>>>(a);
+        CU_LAUNCH(ctx);
+        return MLPG_OK;
+    };
+    if (ctx->opt.rk_order == 0) MLPG_TRY(run(k_assemble_2d<0, 48, 32>, 48, 32));
+    else if (ctx->opt.rk_order == 2) MLPG_TRY(run(k_assemble_2d<2, 48, 32>, 48, 32));
+    else MLPG_TRY(run(k_assemble_2d<1, kMaxS, kChunk>, kMaxS, kChunk));
     return check_flag(ctx, "assembly");
 }
 

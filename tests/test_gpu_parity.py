@@ -290,3 +290,37 @@ def test_full_size_256_two_region_S8():
         f2 += f @ f
     assert np.sqrt(res2 / f2) < 1e-9
     assert st["last_residual"] < 1e-10
+
+
+@pytest.mark.parametrize("order,support", [(0, 2.0), (2, 3.0)])
+def test_rk_orders_forms_and_run(order, support):
+    """RK corrections of order 0 and 2 (Sec. 2.2; order 2 on kernels spanning
+    six neighbours): integrated forms to rounding and a 3-step run in FP64
+    and mixed precision against the oracle at the same order.  The wider
+    kernels make L_m ill-conditioned (smallest/largest singular value near
+    5e-5 here), so the inner GMRES restarts every 32 steps, not 20."""
+    prob = mi.make_problem(f"2d-rk{order}", 10, 2, 4, 1100 + order, 1.0, 0.5, 1.0, 0.01, 3, support=support)
+    solver = dict(inner_restart=32, mixed_restart=32, max_inner=5000)
+    disc = O.Discretization(prob.x, prob.R, prob.lo, prob.hi, rk_order=order)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    with pkg.TransportProblem.from_problem(prob, rk_order=order, inner_tol=1e-12, outer_tol=1e-12, **solver) as tp:
+        tp.integrate().assemble()
+        mats, vecs = tp.forms()
+        ref_m = np.concatenate([F["M0"][None], F["Mt"][None], F["Ms"][None], F["G"], F["Gt"], F["Gs"],
+                                F["K"].reshape(4, -1), F["S"]])
+        for k in range(ref_m.shape[0]):
+            assert np.abs(mats[k] - ref_m[k]).max() <= 1e-12 * np.abs(ref_m[k]).max(), k
+        tr = O.Transport(disc, F, prob.omega, prob.w)
+        Psi, Phi, _ = O.Solver(tr, outer_tol=1e-13).run(np.zeros((tr.M, disc.n)), prob.dt, prob.steps)
+        ref = disc.interpolation_matrix() @ Phi
+        assert _rel(tp.run(prob.dt, prob.steps), ref) < 1e-9
+    with pkg.TransportProblem.from_problem(prob, rk_order=order, precision=pkg.MLPG_MIXED, refine_tol=1e-12,
+                                           **solver) as tp:
+        tp.integrate().assemble()
+        assert _rel(tp.run(prob.dt, prob.steps), ref) < 1e-8
+
+
+def test_rk_order_must_be_linear_in_3d():
+    prob = mi.lognormal_3d(4, sn=4, steps=1)
+    with pytest.raises(pkg.MlpgError):
+        pkg.TransportProblem.from_problem(prob, rk_order=2)
