@@ -70,6 +70,9 @@ typedef struct {
     int mixed_half_prec;   /* MLPG_MIXED: 1 = the FP32 correction solves use the block-Jacobi
                               inverses stored in FP16 (scaled by a power of two per block and
                               direction), 0 = FP32 inverses; default 1 */
+    int outer_method;      /* scattering solve: 0 = GMRES on Phi (Eq. krylov-operator), 1 = source
+                              iteration Phi <- b_phi + D L^-1 MS Phi, stopped when the update is
+                              below outer_tol of Phi (max_outer iterations); default 0 */
     int rk_order;          /* order of the RK correction (Sec. 2.2): 0 (constants reproduced),
                               1 (linear) or 2 (quadratic; needs kernels spanning at least five
                               neighbours, e.g. extent 2.5-3 point spacings); 3D: 1 only;

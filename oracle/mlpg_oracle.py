@@ -486,8 +486,12 @@ class Solver:
     """Backward-Euler time stepping with the nested solve of Sec. 4.2."""
 
     def __init__(self, tr: Transport, outer_tol=1e-13, outer_restart=200, outer_maxit=2000,
-                 inner="lu", inner_tol=1e-13, inner_restart=50):
+                 inner="lu", inner_tol=1e-13, inner_restart=50, outer="gmres"):
+        """outer: "gmres" (the paper's Krylov solve on Phi, Eq. krylov-operator) or
+        "source-iteration" (Phi <- b_phi + D L^-1 MS Phi until the update is
+        below outer_tol of Phi)."""
         self.tr = tr
+        self.outer = outer
         self.outer_tol = outer_tol
         self.outer_restart = outer_restart
         self.outer_maxit = outer_maxit
@@ -529,6 +533,16 @@ class Solver:
         def A(Phi):                                 # (I - D L^-1 MS) Phi
             return Phi - tr.D(self._Linv(tr.MS(Phi)))
         x0 = np.zeros(tr.d.n) if Phi_guess is None else Phi_guess
+        if self.outer == "source-iteration":
+            Phi = np.array(x0, dtype=np.float64, copy=True)
+            for its in range(1, self.outer_maxit + 1):
+                x = self._Linv(tr.MS(Phi))          # L^-1 MS Phi_k
+                new = b_phi + tr.D(x)               # Phi_{k+1}
+                res = np.linalg.norm(new - Phi) / max(np.linalg.norm(new), 1e-300)
+                Phi = new
+                if res <= self.outer_tol:
+                    break
+            return x + b_psi, Phi, StepStats(its, res)   # D Psi = Phi_{k+1}
         Phi, its, res = gmres(A, b_phi, x0, self.outer_tol, self.outer_restart, self.outer_maxit)
         Psi = self._Linv(tr.MS(Phi)) + b_psi        # angular recovery
         return Psi, Phi, StepStats(its, res)

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("refine_tol", ctypes.c_double), ("max_refine", ctypes.c_int),
                 ("mixed_inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("mixed_restart", ctypes.c_int), ("mixed_reorth", ctypes.c_int),
-                ("mixed_half_prec", ctypes.c_int), ("rk_order", ctypes.c_int),
+                ("mixed_half_prec", ctypes.c_int), ("outer_method", ctypes.c_int), ("rk_order", ctypes.c_int),
                 ("stream", ctypes.c_void_p)]
 
 

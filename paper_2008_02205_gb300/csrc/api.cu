@@ -69,6 +69,7 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
         opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART ||
         (opt->mixed_reorth != 0 && opt->mixed_reorth != 1) ||
         (opt->mixed_half_prec != 0 && opt->mixed_half_prec != 1) || opt->rk_order < 0 || opt->rk_order > 2 ||
+        (opt->outer_method != 0 && opt->outer_method != 1) ||
         (opt->dim == 3 && opt->rk_order != 1) || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
@@ -213,6 +214,7 @@ void mlpg_default_options(mlpg_options *o) {
     o->mixed_restart = 20;
     o->mixed_reorth = 0;
     o->mixed_half_prec = 1;
+    o->outer_method = 0;
     o->rk_order = 1;
     o->stream = nullptr;
 }

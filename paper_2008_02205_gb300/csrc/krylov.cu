@@ -379,6 +379,19 @@ __global__ void k_bank_combine(int64_t N, int kmax, const T *__restrict__ bank,
 }
 
 // total += sum_m its[m]  (one warp)
+__global__ void k_bump(long long *__restrict__ c) { *c += 1; }
+
+// source-iteration update: d <- b_phi + d (the new Phi), e <- d - phi, phi <- d
+__global__ void k_si_update(int64_t n, const double *__restrict__ bphi, double *__restrict__ d,
+                            double *__restrict__ phi, double *__restrict__ e) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = bphi[i] + d[i];
+    e[i] = v - phi[i];
+    phi[i] = v;
+    d[i] = v;
+}
+
 __global__ void k_add_its(int M, const int *__restrict__ its, long long *__restrict__ total) {
     long long s = 0;
     for (int m = threadIdx.x; m < M; m += 32) s += its[m];
@@ -706,6 +719,8 @@ static mlpg_status outer_bank(mlpg_ctx *ctx, int R, T **bank, T **xacc) {
 // Nested solve of (L - MS D) Psi = f (Sec. 4.2): first flight, GMRES on Phi,
 // recovery.  f and Psi are FP64 [n][m]; inner solves run in T.  Phi_io holds
 // the initial guess of Phi on entry (may be null) and the result on exit.
+static mlpg_status global_norm(mlpg_ctx *ctx, const double *a, int64_t N, double *out_host_slot);
+
 template <typename T>
 static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out, double *Phi_io,
                                 double inner_tol, double outer_tol) {
@@ -732,6 +747,37 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     MLPG_TRY(gmres_alloc(ctx, ctx->gout, n, 1, ctx->opt.outer_restart));
     if (Phi_io) CU(ctx, cudaMemcpyAsync(phi, Phi_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else CU(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, s));
+    if (ctx->opt.outer_method == 1) {
+        // source iteration: Phi <- b_phi + D L^-1 MS Phi, one transport solve per
+        // iteration.  Psi = L^-1 MS Phi_k + b_psi satisfies D Psi = Phi_{k+1}.
+        // In a mixed-precision correction (T = float) the iterate reached after
+        // outer_restart iterations is kept, as for the GMRES outer solve.
+        double *e = ctx->nvec + 4 * n;
+        const bool correction = sizeof(T) == 4;
+        const int cap = correction ? ctx->opt.outer_restart : ctx->opt.max_outer;
+        for (int k = 0;; ++k) {
+            MLPG_TRY(apply_MS<T>(ctx, phi, rhs));
+            MLPG_TRY(inner_solve<T>(ctx, rhs, x, inner_tol));
+            k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, x, d);
+            CU_LAUNCH(ctx);
+            k_si_update<<<nblk(n), kBlock, 0, s>>>(n, bphi, d, phi, e);
+            CU_LAUNCH(ctx);
+            k_bump<<<1, 1, 0, s>>>(ctx->d_its + 1);
+            CU_LAUNCH(ctx);
+            MLPG_TRY(global_norm(ctx, e, n, ctx->h_red + 4));
+            MLPG_TRY(global_norm(ctx, phi, n, ctx->h_red + 5));
+            CU(ctx, cudaStreamSynchronize(s));
+            if (std::sqrt(ctx->h_red[4]) <= outer_tol * std::sqrt(ctx->h_red[5])) break;
+            if (k + 1 >= cap) {
+                if (correction) break;
+                return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "source iteration reached its iteration cap");
+            }
+        }
+        k_add<T, T><<<nblk(N), kBlock, 0, s>>>(N, x, bpsi, Psi_out);
+        CU_LAUNCH(ctx);
+        if (Phi_io) CU(ctx, cudaMemcpyAsync(Phi_io, phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        return MLPG_OK;
+    }
     // Each operator apply solves x = L^{-1} MS v for one outer basis vector v.
     // Those solutions are kept (bank) so that L^{-1} MS Phi, needed for the
     // angular recovery Psi = L^{-1} MS Phi + b_psi, is the same combination of

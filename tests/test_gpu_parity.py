@@ -324,3 +324,17 @@ def test_rk_order_must_be_linear_in_3d():
     prob = mi.lognormal_3d(4, sn=4, steps=1)
     with pytest.raises(pkg.MlpgError):
         pkg.TransportProblem.from_problem(prob, rk_order=2)
+
+
+@pytest.mark.parametrize("precision,tol", [(pkg.MLPG_FP64, 1e-9), (pkg.MLPG_MIXED, 1e-8)])
+def test_source_iteration_outer(precision, tol):
+    """Source iteration for the scattering solve (outer_method = 1): the same
+    fluxes as the oracle's Krylov solve."""
+    prob = mi.small_2d(16, sn=4, seed=1004, steps=3)
+    ref, *_ = _oracle_run(prob)
+    with pkg.TransportProblem.from_problem(prob, precision=precision, outer_method=1, inner_tol=1e-13,
+                                           outer_tol=1e-13, refine_tol=1e-12) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+        assert _rel(phi, ref) < tol
+        assert tp.stats()["last_outer_iters"] > 1

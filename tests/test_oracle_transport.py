@@ -171,3 +171,22 @@ def test_planted_missing_supg_sigma_term_breaks_mms(monkeypatch):
         x, h = mi.jittered_lattice(n, 2, 5, lo=-1, hi=1, jitter=0.0)
         errs.append(mms.mms_run(mms.Sinusoidal(), x, np.full(len(x), 2 * h), om, w))
     assert errs[1] > 2e-3 or np.log2(errs[0] / errs[1]) < 1.5
+
+
+@pytest.mark.parametrize("ratio", [0.5, 0.9])
+def test_source_iteration_converges_to_the_krylov_solution(ratio):
+    # the same step by source iteration: the fixed point of Phi <- b_phi + D L^-1 MS Phi;
+    # in a nearly infinite medium its error contracts by about the scattering ratio per
+    # iteration, so it needs about log(tol)/log(c) iterations where GMRES needs few
+    p = mi.small_2d(10, sn=4, seed=1000, sigma_t=4.0, sigma_s=4.0 * ratio)
+    d = O.Discretization(p.x, p.R)
+    F = d.assemble_per_point(p.sigma_t, p.sigma_s, p.q)
+    tr = O.Transport(d, F, p.omega, p.w)
+    Psi0 = np.random.default_rng(1).uniform(0, 1, (tr.M, d.n))
+    Pg, Fg, sg = O.Solver(tr, outer_tol=1e-13).step(Psi0, p.dt)
+    Ps, Fs, ss = O.Solver(tr, outer_tol=1e-13, outer="source-iteration").step(Psi0, p.dt)
+    assert np.linalg.norm(Fs - Fg) / np.linalg.norm(Fg) < 1e-11
+    assert np.linalg.norm(Ps - Pg) / np.linalg.norm(Pg) < 1e-11
+    assert np.abs(tr.D(Ps) - Fs).max() < 1e-13 * np.abs(Fs).max()
+    assert ss.outer_iterations <= math.log(1e-13) / math.log(ratio) + 5
+    assert ss.outer_iterations > sg.outer_iterations
