@@ -296,21 +296,8 @@ mlpg_status mlpg_integrate(mlpg_ctx *ctx) {
             ctx->state = 1;
             return MLPG_OK;
         }
-        HostCells cells;
-        int64_t bad = build_cells_2d(ctx->n, ctx->h_x.data(), ctx->h_R.data(), ctx->opt.lo, ctx->opt.hi,
-                                     ctx->h_rowptr.data(), ctx->h_col.data(), 25, 5, cells);
-        if (bad >= 0) return set_err(ctx, MLPG_ERR_GEOMETRY, "empty cell at point " + std::to_string(bad));
-        ctx->nverts = (int64_t)cells.labels.size();
-        ctx->nvq = cells.n_volume_qp;
-        ctx->nbq = cells.n_boundary_qp;
-        MLPG_TRY(dalloc(ctx, &ctx->cptr, ctx->n + 1));
-        MLPG_TRY(dalloc(ctx, &ctx->verts, 2 * ctx->nverts));
-        MLPG_TRY(dalloc(ctx, &ctx->labels, ctx->nverts));
-        cudaStream_t s = ctx->stream;
-        CU(ctx, cudaMemcpyAsync(ctx->cptr, cells.cptr.data(), (ctx->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        CU(ctx, cudaMemcpyAsync(ctx->verts, cells.verts.data(), 2 * ctx->nverts * sizeof(double), cudaMemcpyHostToDevice, s));
-        CU(ctx, cudaMemcpyAsync(ctx->labels, cells.labels.data(), ctx->nverts * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        CU(ctx, cudaMemcpyAsync(ctx->V, cells.volume.data(), ctx->n * sizeof(double), cudaMemcpyHostToDevice, s));
+        // 2D cells on the device: 25-point triangle rule, 5-point edge rule
+        MLPG_TRY(run_cells_2d(ctx, 25, 5));
         MLPG_TRY(run_interp(ctx));  // synchronises
         MLPG_TRY(build_blocks(ctx));
         ctx->st.nnz = ctx->nnz;

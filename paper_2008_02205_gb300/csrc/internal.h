@@ -37,18 +37,7 @@ mlpg_status cuda_fail(mlpg_ctx *ctx, cudaError_t e, const char *what, const char
     } while (0)
 
 // host geometry (geometry.cpp) ----------------------------------------------
-struct HostCells {
-    std::vector<int32_t> cptr;      // n + 1
-    std::vector<double> verts;      // 2 * nv
-    std::vector<int32_t> labels;    // nv: >= 0 bisector, -(f+1) domain face, LABEL_EXTENT
-    std::vector<double> volume;     // n
-    int64_t n_volume_qp = 0, n_boundary_qp = 0;
-};
 constexpr int32_t kLabelExtent = -100;
-// Builds the cells of all points; returns the index of a failing cell or -1.
-int64_t build_cells_2d(int64_t n, const double *x, const double *R, const double *lo,
-                       const double *hi, const int32_t *rowptr, const int32_t *col,
-                       int tri_points, int line_points, HostCells &out);
 // 3D cells as flat element lists: tetrahedra (generator of `owner`, three
 // stored vertices) and boundary triangles (three stored vertices, box face).
 struct HostCells3 {
@@ -212,6 +201,7 @@ mlpg_status dalloc(mlpg_ctx *ctx, T **p, size_t count) {
 
 // kernels / launchers (neighbors.cu, assemble.cu, operators.cu, krylov.cu)
 mlpg_status run_neighbors(mlpg_ctx *ctx);
+mlpg_status run_cells_2d(mlpg_ctx *ctx, int tri_points, int line_points);
 mlpg_status run_interp(mlpg_ctx *ctx);
 mlpg_status run_assemble(mlpg_ctx *ctx);
 mlpg_status run_interp_3d(mlpg_ctx *ctx);
