@@ -326,7 +326,25 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
     }
     const int32_t p1 = rowptr[row + 1];
     int32_t p = rowptr[row];
-    for (; p + 1 < p1; p += 2) {   // two entries in flight
+    if constexpr (K == 6) {   // 2D: the six values in named registers (schedules best)
+        for (; p + 1 < p1; p += 2) {   // two entries in flight
+            const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)lane, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)lane;
+            const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
+                        a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
+            const float b0 = A32[p + 1], b1 = A32[nnz + p + 1], b2 = A32[2 * nnz + p + 1],
+                        b3 = A32[3 * nnz + p + 1], b4 = A32[4 * nnz + p + 1], b5 = A32[5 * nnz + p + 1];
+#pragma unroll
+            for (int t = 0; t < DPL; ++t) {
+                if (on[t]) {
+                    const float x0 = X[jb0 + t * TM], x1 = X[jb1 + t * TM];
+                    float v0 = fmaf(c[5][t], a5, fmaf(c[4][t], a4, fmaf(c[3][t], a3, fmaf(c[2][t], a2, fmaf(c[1][t], a1, a0)))));
+                    float v1 = fmaf(c[5][t], b5, fmaf(c[4][t], b4, fmaf(c[3][t], b3, fmaf(c[2][t], b2, fmaf(c[1][t], b1, b0)))));
+                    acc[t] = fmaf(v1, x1, fmaf(v0, x0, acc[t]));
+                }
+            }
+        }
+    }
+    for (; p + 1 < p1; p += 2) {   // two entries in flight (generic number of arrays)
         const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)lane, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)lane;
         float a[K], b[K];
 #pragma unroll
