@@ -130,7 +130,7 @@ def _traffic():
         return None
     vals = {}
     for line in txt.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_sha256")):
+        if ":" in line and line.strip().lstrip("-* ").startswith(("traffic_bytes_per_launch", "source_sha256")):
             k, v = line.split(":", 1)
             vals[k.strip(" -`*")] = v.strip(" `*")
     if vals.get("source_sha256") != src:

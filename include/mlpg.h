@@ -59,7 +59,7 @@ typedef struct {
     double refine_tol;     /* MLPG_MIXED: FP64 step residual ||R|| <= tol ||f||; default 1e-11 */
     int max_refine;        /* MLPG_MIXED: refinement sweeps per step; default 12 */
     double mixed_inner_tol;/* MLPG_MIXED: tolerance of the FP32 correction solves; default 1e-2 */
-    int check_every;       /* inner GMRES: host convergence check interval (steps); default 4 */
+    int check_every;       /* inner GMRES: host convergence check interval (steps); default 3 */
     int mixed_restart;     /* MLPG_MIXED: restart length of the FP32 inner GMRES (<= 32); default 20.
                               The FP32 correction solves keep the iterate reached at their iteration
                               caps (max_inner; one outer restart cycle): the FP64 step residual alone

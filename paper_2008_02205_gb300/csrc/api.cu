@@ -210,7 +210,7 @@ void mlpg_default_options(mlpg_options *o) {
     o->refine_tol = 1e-11;
     o->max_refine = 12;
     o->mixed_inner_tol = 1e-2;
-    o->check_every = 4;
+    o->check_every = 3;
     o->mixed_restart = 20;
     o->mixed_reorth = 0;
     o->mixed_half_prec = 1;

@@ -88,6 +88,6 @@ def test_binding_structs_match_header_layout(tmp_path, struct, cls):
 def test_default_options(lib):
     import paper_2008_02205_gb300 as pkg
     o = pkg.mlpg_default_options()
-    assert (o.precision, o.inner_restart, o.mixed_restart, o.check_every) == (0, 20, 20, 4)
+    assert (o.precision, o.inner_restart, o.mixed_restart, o.check_every) == (0, 20, 20, 3)
     assert (o.mixed_reorth, o.mixed_half_prec, o.rk_order) == (0, 1, 1)
     assert (o.inner_tol, o.outer_tol, o.mixed_inner_tol) == (1e-12, 1e-12, 1e-2)
