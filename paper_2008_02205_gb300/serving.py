@@ -1,0 +1,151 @@
+"""Continuous-batching serving loop over independent transport problems.
+
+Requests (a point set, its quadrature and materials, a number of backward-
+Euler steps) arrive over time.  The loop admits arrived requests in order
+while the device memory they are estimated to need fits the budget and a
+slot is free, keeps every admitted problem's operators and flux state
+resident on the device, and advances all admitted problems together: each
+iteration is one ``mlpg_step_batch`` call, which steps every context on its
+own stream so that their kernels overlap.  A problem leaves as soon as its
+last step is done (its memory and slot go to the next arrivals), with its
+latency measured from its arrival.  All compute goes through the C ABI; this
+module only schedules.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Request:
+    problem: object             # an mlpg_inputs.Problem (or anything the backend accepts)
+    steps: int
+    dt: float
+    arrival: float = 0.0        # seconds after the start of the run
+    options: dict = field(default_factory=dict)
+
+
+@dataclass
+class Result:
+    request: Request
+    flux: np.ndarray | None = None
+    admitted: float = 0.0
+    finished: float = 0.0
+    error: str | None = None
+
+    @property
+    def latency(self):
+        return self.finished - self.request.arrival
+
+
+def estimate_bytes(problem, precision_mixed: bool = True, restart: int = 20) -> int:
+    """Device memory of one problem, from its size: the overlap pattern (mean
+    row length from the kernel extents), the integrated forms, the operator
+    arrays, the materialised FP64 operator, the block inverses and the Krylov
+    vectors.  An admission estimate, not an allocation count."""
+    x = np.asarray(problem.x)
+    n, dim = x.shape
+    m = len(problem.w)
+    R = float(np.mean(problem.R))
+    ball = math.pi * (2 * R) ** 2 if dim == 2 else 4.0 / 3.0 * math.pi * (2 * R) ** 3
+    nnz = n * min(n, max(1.0, ball * n))
+    nmats = 3 + 3 * dim + dim * dim + 2 * dim
+    K = 1 + dim + dim * (dim + 1) // 2
+    b = nnz * (4 + 8 * nmats + 12 * K + 8 * m)          # pattern, forms, A64/A32, L64
+    b += n * m * 16 * (4 + (2 if precision_mixed else 0))  # block inverses (+ FP16 copy)
+    vec = 4 if precision_mixed else 8
+    b += n * m * (vec * (restart + 4) + 8 * 8)            # Krylov basis + FP64 state/work
+    return int(b)
+
+
+class LibraryBackend:
+    """Runs requests on the GPU library through ``TransportProblem``."""
+
+    def __init__(self):
+        import paper_2008_02205_gb300 as pkg
+        self.pkg = pkg
+
+    def open(self, req: Request):
+        tp = self.pkg.TransportProblem.from_problem(req.problem, **req.options)
+        tp.integrate().assemble()
+        return tp
+
+    def step(self, handles, dts):
+        self.pkg.mlpg_step_batch([h.ctx for h in handles], dts)
+
+    def flux(self, h):
+        return h.scalar_flux()
+
+    def close(self, h):
+        h.close()
+
+
+class Server:
+    """FIFO admission under a device-memory budget and a slot limit; one
+    concurrent step of every admitted problem per iteration."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 16, backend=None, clock=time.perf_counter,
+                 estimate=estimate_bytes, sleep=time.sleep):
+        self.budget = int(hbm_budget_bytes)
+        self.max_active = int(max_active)
+        self.backend = backend if backend is not None else LibraryBackend()
+        self.clock = clock
+        self.estimate = estimate
+        self.sleep = sleep
+        self.peak_active = 0
+        self.iterations = 0
+
+    def run(self, requests):
+        pending = sorted(requests, key=lambda r: r.arrival)
+        results = {id(r): Result(r) for r in requests}
+        active = []          # [request, handle, bytes, steps done]
+        used = 0
+        t0 = self.clock()
+        while pending or active:
+            now = self.clock() - t0
+            while pending and pending[0].arrival <= now and len(active) < self.max_active:
+                req = pending[0]
+                need = self.estimate(req.problem, req.options.get("precision", 0) == 1)   # 1: mixed
+                if need > self.budget:      # can never fit: refuse it
+                    pending.pop(0)
+                    res = results[id(req)]
+                    res.error = f"needs {need} bytes, budget {self.budget}"
+                    res.admitted = res.finished = now
+                    continue
+                if used + need > self.budget:
+                    break                   # wait for memory to free up (FIFO)
+                pending.pop(0)
+                results[id(req)].admitted = self.clock() - t0
+                active.append([req, self.backend.open(req), need, 0])
+                used += need
+            if not active:
+                if pending:                 # idle until the next arrival
+                    wait = pending[0].arrival - (self.clock() - t0)
+                    if wait > 0:
+                        self.sleep(min(wait, 0.01))
+                continue
+            self.peak_active = max(self.peak_active, len(active))
+            self.backend.step([a[1] for a in active], [a[0].dt for a in active])
+            self.iterations += 1
+            keep = []
+            for a in active:
+                a[3] += 1
+                if a[3] >= a[0].steps:
+                    res = results[id(a[0])]
+                    res.flux = self.backend.flux(a[1])
+                    self.backend.close(a[1])
+                    res.finished = self.clock() - t0
+                    used -= a[2]
+                else:
+                    keep.append(a)
+            active = keep
+        return [results[id(r)] for r in requests]
+
+
+def latency_percentiles(results, qs=(50, 99)):
+    lat = np.array([r.latency for r in results if r.error is None])
+    return {f"p{q}": float(np.percentile(lat, q)) for q in qs} if len(lat) else {}
