@@ -45,7 +45,7 @@ typedef enum {
 } mlpg_precision;
 
 typedef struct {
-    int dim;               /* spatial dimension: 2 */
+    int dim;               /* spatial dimension: 2 (polygonal cells) or 3 (polyhedral cells); default 2 */
     double lo[3], hi[3];   /* axis-aligned box domain */
     double tau_factor;     /* SUPG tau_i = tau_factor * h_i, h_i = R_i / 2 (Sec. 4.1); default 1 */
     double c;              /* speed of light in 1/(c dt) (Sec. 4.1); default 1 */
@@ -122,7 +122,8 @@ mlpg_status mlpg_create_dev(const mlpg_options *opt, int64_t n, const double *po
                             const double *q, mlpg_ctx **out);
 
 /* Incoming isotropic angular flux psi_b on box face `face` (0:-x 1:+x 2:-y
- * 3:+y), Eq. rad-boundary.  Default 0 (vacuum).  Any state after create. */
+ * 3:+y, in 3D also 4:-z 5:+z), Eq. rad-boundary.  Default 0 (vacuum).  Any
+ * state after create. */
 mlpg_status mlpg_set_inflow(mlpg_ctx *ctx, int face, double psi_b);
 
 /* Initial angular flux coefficients Psi_i(0) = psi_init(x_i) (Sec. 4.1), host
@@ -130,9 +131,11 @@ mlpg_status mlpg_set_inflow(mlpg_ctx *ctx, int face, double psi_b);
 mlpg_status mlpg_set_initial(mlpg_ctx *ctx, const double *psi0);
 
 /* Neighbour search (Sec. 3.4, overlap connectivity), Voronoi-like cells and
- * their quadrature points (Sec. 3.1-3.2, App. A), RK point interpolation at
- * the centres (Eq. flux-expansion).  MLPG_ERR_RK_SINGULAR if an RK moment
- * matrix is singular, MLPG_ERR_GEOMETRY if a cell is empty. */
+ * their quadrature points (Sec. 3.1-3.2, App. A; 2D cells clipped on the
+ * device, 3D cells on the host cores), RK point interpolation at the centres
+ * (Eq. flux-expansion).  MLPG_ERR_RK_SINGULAR if an RK moment matrix is
+ * singular, MLPG_ERR_GEOMETRY if a cell is empty, MLPG_ERR_ARG if more
+ * functions reach one cell or element than the integration kernels hold. */
 mlpg_status mlpg_integrate(mlpg_ctx *ctx);
 
 /* Quadrature-outermost integration of every bilinear / linear form of the
@@ -140,10 +143,13 @@ mlpg_status mlpg_integrate(mlpg_ctx *ctx);
 mlpg_status mlpg_assemble(mlpg_ctx *ctx);
 
 /* One backward-Euler step (Sec. 4.1) solved as in Sec. 4.2: first-flight
- * batched transport solves, GMRES on the scalar-flux coefficients
- * (Eq. krylov-operator) whose operator applies the batched transport solve,
- * angular recovery.  dt = INFINITY solves the steady problem.  Changing dt
- * only re-forms the operators.  MLPG_ERR_NOT_CONVERGED on an iteration cap. */
+ * batched transport solves, GMRES (or source iteration, outer_method) on the
+ * scalar-flux coefficients (Eq. krylov-operator) whose operator applies the
+ * batched transport solve, angular recovery.  MLPG_MIXED wraps this in FP64
+ * iterative refinement of the step with FP32 corrections.  dt = INFINITY
+ * solves the steady problem.  Changing dt only re-forms the operators.
+ * MLPG_ERR_NOT_CONVERGED on an FP64 iteration cap or when the refinement does
+ * not converge in max_refine sweeps. */
 mlpg_status mlpg_step(mlpg_ctx *ctx, double dt);
 
 /* One backward-Euler step (as mlpg_step) of each of `count` independent
