@@ -17,7 +17,10 @@ def test_served_results_equal_alone_results():
     probs = mi.batched_2d(3, seed=4200, n_range=(64, 300), steps=3) + \
         [mi.lognormal_3d(6, sn=4, seed=3002, steps=3, dt=0.02)]
     opts = dict(precision=pkg.MLPG_MIXED, refine_tol=1e-12)
-    reqs = [Request(p, p.steps, p.dt, arrival=0.02 * k, options=opts) for k, p in enumerate(probs)]
+    # the first two arrive together (the budget below admits any two, so they
+    # overlap on the device whatever the timing); the others join later
+    arrivals = [0.0, 0.0, 0.02, 0.04]
+    reqs = [Request(p, p.steps, p.dt, arrival=t, options=opts) for p, t in zip(probs, arrivals)]
     alone = []
     for r in reqs:
         with pkg.TransportProblem.from_problem(r.problem, **r.options) as tp:
