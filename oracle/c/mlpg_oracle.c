@@ -788,6 +788,8 @@ static int rk_eval(int dim, int order, const double *xe, double s, int ncand, co
                    const double *x, const double *R, const double *V, int32_t *idx, double *U,
                    double *dU)
 {
+    /* per-call work arrays kept in static storage (about 330 KB): the oracle is
+     * single-threaded (process pools start separate processes), so one copy serves */
     static double W[1024], dW[1024][3], P[1024][10], dPa[1024][3][10];
     double M[100] = {0}, dM[3][100] = {{0}};
     int ns = 0, np = 1;
