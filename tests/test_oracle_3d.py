@@ -240,3 +240,19 @@ def test_infinite_medium_recurrence_3d(nref):
         Psi, Phi, _ = s.step(Psi, p.dt, Phi_guess=Phi)
         assert np.abs(I @ Phi - ph).max() / ph < defect
     assert defect < (2.5e-2 if nref == 2 else 5e-3)
+
+
+def test_manufactured_solution_converges_3d():
+    # the sinusoidal manufactured solution of Sec. 5.1 in 3D (steady, S4, regular
+    # lattices on [-1, 1]^3): at least second order in space (measured about 3)
+    from oracle import mms
+    om, w = mi.level_symmetric(4, 3)
+    errs = []
+    for n in (4, 6, 8):
+        x, h = mi.jittered_lattice(n, 3, 5, lo=-1, hi=1, jitter=0.0)
+        errs.append(mms.mms_run(mms.Sinusoidal(), x, np.full(len(x), 2 * h), om, w))
+    errs = np.array(errs)
+    hs = 2.0 / np.array([4, 6, 8])
+    slopes = np.log(errs[:-1] / errs[1:]) / np.log(hs[:-1] / hs[1:])
+    assert slopes.min() > 2.0, slopes
+    assert errs[-1] < 5e-3
