@@ -358,3 +358,50 @@ def cone_hits(axis=(1.0, 0.0, 0.0), half_angle_deg: float = 15.0):
     ax = np.asarray(axis, float) / np.linalg.norm(axis)
     c = np.cos(np.radians(half_angle_deg))
     return lambda o: float(np.asarray(o) @ ax) >= c
+
+
+# ---------------------------------------------------------------------------
+# line source and absorbing disk (the asteroid problem, Sec. 5.4, scaled down)
+# ---------------------------------------------------------------------------
+def polar_product_quadrature(n_azimuth: int, n_polar: int):
+    """Product set for line-source problems: in-plane lengths mu_k (the cosine
+    of the angle to the x-y plane) at the Gauss-Legendre nodes of [0, 1] with
+    weights a_k, times n_azimuth equally spaced azimuths (offset by half a
+    spacing); Omega = (mu cos theta, mu sin theta, sqrt(1 - mu^2)).  The weight
+    of an ordinate is 2 pi mu_k a_k / n_azimuth: with the azimuths resolved,
+    the scalar flux of a unit line source is then sum_k a_k exp(-omega / mu_k) / r,
+    the polar quadrature of the mu integral in App. B (which integrates over mu
+    with unit measure).  Returns (omega[M, 3], w[M], mu[K], a[K])."""
+    t, a = np.polynomial.legendre.leggauss(n_polar)
+    mu, a = 0.5 * (t + 1.0), 0.5 * a
+    th = (np.arange(n_azimuth) + 0.5) * (2.0 * math.pi / n_azimuth)
+    om = np.array([[m * math.cos(p), m * math.sin(p), math.sqrt(1.0 - m * m)] for m in mu for p in th])
+    w = np.repeat(2.0 * math.pi * mu * a / n_azimuth, n_azimuth)
+    return om, w, mu, a
+
+
+def asteroid_2d(n_per_dim: int = 32, n_azimuth: int = 64, n_polar: int = 2,
+                sigma_background: float = 0.5, sigma_asteroid: float = 10.0,
+                radius: float = 0.35, centre=(0.35, 0.0), source=(-0.55, 0.0),
+                source_width: float = 0.1):
+    """A scaled-down 2D asteroid problem on [-1, 1]^2: a disk of radius
+    `radius` at `centre` with sigma_t = sigma_asteroid for the points inside it
+    and sigma_background elsewhere, no scattering, an isotropic source
+    q = exp(-|x - source|^2 / (2 source_width^2)) per point, cut to zero beyond
+    three widths,
+    vacuum boundaries, one steady step, the product set of
+    polar_product_quadrature.  Regular lattice (no jitter), so every interior
+    cell is an h x h square and a source point j carries q_j h^2.  Defaults:
+    32x32 points, 64 azimuths x 2 polar levels, sigma 0.5 / 10, a disk 7 mean
+    free paths across at 0.55 from a source of width 0.1.  The paper's problem
+    (radius 35, source 70 from the surface, sigma 0.001 / 10, a shell with
+    variable spacing and a refined 4,096-ordinate set) is not reproduced."""
+    x, h = jittered_lattice(n_per_dim, 2, 0, lo=-1.0, hi=1.0, jitter=0.0)
+    inside = np.linalg.norm(x - np.asarray(centre, np.float64), axis=1) < radius
+    st = np.where(inside, float(sigma_asteroid), float(sigma_background))
+    d2 = np.sum((x - np.asarray(source, np.float64)) ** 2, axis=1) / source_width ** 2
+    q = np.where(d2 <= 9.0, np.exp(-0.5 * d2), 0.0)
+    omega, w, _, _ = polar_product_quadrature(n_azimuth, n_polar)
+    return Problem(name=f"2d-asteroid-{n_per_dim}x{n_per_dim}-A{n_azimuth}P{n_polar}", dim=2, x=x,
+                   R=np.full(len(x), 2.0 * h), omega=omega, w=w, sigma_t=st, sigma_s=np.zeros(len(x)),
+                   q=q, dt=math.inf, steps=1, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), spacing=h)

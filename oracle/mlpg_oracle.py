@@ -15,7 +15,8 @@ Split of work:
     the unpreconditioned GMRES on the scalar flux (Eq. krylov-operator), the
     angular recovery solve, backward-Euler time stepping (Sec. 4.1), the
     point-value recovery phi_i = sum_j V_j U_j(x_i) Phi_j (Eq. flux-expansion)
-    and the manufactured sources of Sec. 5.1.
+    and the manufactured sources of Sec. 5.1 (``mms.py``).
+  * ``asteroid.py``: the analytic line-source solution of App. B.
 
 Inner inverses L_m^{-1} are exact sparse LU solves (a linear solve has a plain
 definition; the paper's GMRES + ILUT reaches the same result up to its
