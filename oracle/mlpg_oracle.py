@@ -23,7 +23,10 @@ definition; the paper's GMRES + ILUT reaches the same result up to its
 tolerance).  ``inner="ilut-gmres"`` runs the paper's own inner scheme instead
 (restarted GMRES, right preconditioned by an incomplete LU with threshold) to
 report iteration counts.  The outer scattering solve is the paper's
-unpreconditioned GMRES.  ``step_direct`` solves the coupled step system
+unpreconditioned GMRES; ``precond="dsa"`` right-preconditions it with a
+diffusion correction built from the same forms (not in the paper, which names
+diffusion acceleration as future work), or source iteration replaces it.
+``step_direct`` solves the coupled step system
 (L - MS D) Psi = T Psi^{n-1} + r with one sparse LU and pins the nested scheme.
 
 Unpinned parts: individual off-diagonal values of the SUPG forms have no
@@ -423,6 +426,28 @@ class Transport:
     def D(self, Psi):
         return self.w @ Psi
 
+    # low-order diffusion operator for the DSA-like preconditioner ----------
+    def sigma_t_rows(self):
+        """Test-function average of sigma_t per row: (Mt 1)_i / (M0 1)_i =
+        int sigma_t v_i / int v_i (the trial functions sum to one)."""
+        one = np.ones(self.d.n)
+        return (self.d.csr(self.F["Mt"]) @ one) / (self.d.csr(self.F["M0"]) @ one)
+
+    def diffusion_matrix(self, kappa):
+        """Galerkin P1-diffusion operator on the same pattern, from the forms
+        already integrated (the paper names diffusion acceleration as future
+        work, Sec. 6, without deriving one):
+            C = diag(1 / (3 sigma_t_i)) sum_a K_aa + kappa M0 + (Mt - Ms) + 1/2 sum_f S_f,
+        i.e. -div(D grad phi) + (kappa + sigma_a) phi with D = 1 / (3 sigma_t)
+        taken per row, and the Marshak vacuum condition D d_n phi + phi / 2 = 0 on
+        every face."""
+        d, F = self.d, self.F
+        stiff = sum(d.csr(F["K"][a, a]) for a in range(d.dim))
+        C = sp.diags(1.0 / (3.0 * self.sigma_t_rows())) @ stiff
+        C = C + kappa * d.csr(F["M0"]) + d.csr(F["Mt"]) - d.csr(F["Ms"])
+        C = C + 0.5 * sum(d.csr(F["S"][f]) for f in range(2 * d.dim))
+        return C.tocsr()
+
     def MS(self, Phi):
         return np.stack([self._MS[m] @ Phi for m in range(self.M)])
 
@@ -487,12 +512,22 @@ class Solver:
     """Backward-Euler time stepping with the nested solve of Sec. 4.2."""
 
     def __init__(self, tr: Transport, outer_tol=1e-13, outer_restart=200, outer_maxit=2000,
-                 inner="lu", inner_tol=1e-13, inner_restart=50, outer="gmres"):
+                 inner="lu", inner_tol=1e-13, inner_restart=50, outer="gmres", precond=None):
         """outer: "gmres" (the paper's Krylov solve on Phi, Eq. krylov-operator) or
         "source-iteration" (Phi <- b_phi + D L^-1 MS Phi until the update is
-        below outer_tol of Phi)."""
+        below outer_tol of Phi).  precond="dsa" right-preconditions the outer
+        GMRES with P^-1 = I + C^-1 Ms (C: Transport.diffusion_matrix): the
+        scattering source of a Krylov direction drives a diffusion correction,
+        so the slowly converging smooth modes of thick scattering regions are
+        taken out; the solution is the same, the residual tested is the true one."""
+        if precond not in (None, "dsa"):
+            raise ValueError("precond: None or 'dsa'")
+        if precond is not None and outer != "gmres":
+            raise ValueError("the DSA-like preconditioner is for the GMRES outer solve")
         self.tr = tr
         self.outer = outer
+        self.precond = precond
+        self._dsa = None
         self.outer_tol = outer_tol
         self.outer_restart = outer_restart
         self.outer_maxit = outer_maxit
@@ -544,7 +579,13 @@ class Solver:
                 if res <= self.outer_tol:
                     break
             return x + b_psi, Phi, StepStats(its, res)   # D Psi = Phi_{k+1}
-        Phi, its, res = gmres(A, b_phi, x0, self.outer_tol, self.outer_restart, self.outer_maxit)
+        P = None
+        if self.precond == "dsa":
+            if self._dsa is None or self._dsa[0] != kappa:
+                self._dsa = (kappa, spla.splu(tr.diffusion_matrix(kappa).tocsc()), tr.d.csr(tr.F["Ms"]))
+            _, C, Ms = self._dsa
+            P = lambda v: v + C.solve(Ms @ v)
+        Phi, its, res = gmres(A, b_phi, x0, self.outer_tol, self.outer_restart, self.outer_maxit, precond=P)
         Psi = self._Linv(tr.MS(Phi)) + b_psi        # angular recovery
         return Psi, Phi, StepStats(its, res)
 
