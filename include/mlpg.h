@@ -109,7 +109,12 @@ void mlpg_default_options(mlpg_options *opt);
  *   sigma_t[n], sigma_s[n], q[n]
  *                        total / scattering cross sections and isotropic source
  *                        per steradian, constant over each point's cell
- * Host pointers.  Fails with MLPG_ERR_ARG on bad sizes or non-finite values.  */
+ * Host pointers.  Fails with MLPG_ERR_ARG on bad sizes, non-finite values,
+ * non-positive extents or non-unit ordinates, MLPG_ERR_GEOMETRY for a point
+ * outside the box.  *out is NULL when the options or sizes are rejected; a
+ * failure after that (a bad value, a CUDA or allocation error) leaves in *out
+ * a context that holds the message for mlpg_last_error() and must be passed
+ * to mlpg_destroy.  */
 mlpg_status mlpg_create(const mlpg_options *opt, int64_t n, const double *points,
                         const double *kernel_extent, int32_t m, const double *omega,
                         const double *w, const double *sigma_t, const double *sigma_s,

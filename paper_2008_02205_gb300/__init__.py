@@ -134,8 +134,26 @@ def mlpg_default_options(**overrides) -> Options:
     return o
 
 
+def _check_shapes(dim, x, R, om, ww, st, ss, qq):
+    """The C side reads n * dim, n, 3 m and m values from these pointers."""
+    if x.ndim != 2 or x.shape[1] != dim:
+        raise ValueError(f"points must be [n, {dim}], got {x.shape}")
+    if om.ndim != 2 or om.shape[1] != 3:
+        raise ValueError(f"omega must be [m, 3], got {om.shape}")
+    n, m = x.shape[0], om.shape[0]
+    for name, a, k in (("kernel_extent", R, n), ("w", ww, m), ("sigma_t", st, n), ("sigma_s", ss, n), ("q", qq, n)):
+        if a.shape != (k,):
+            raise ValueError(f"{name} must have shape ({k},), got {a.shape}")
+
+
+def _state_size(ctx):
+    s = mlpg_get_stats(ctx)
+    return s["n"] * s["m"]
+
+
 def mlpg_create(opt: Options, points, kernel_extent, omega, w, sigma_t, sigma_s, q):
     x, R, om, ww, st, ss, qq = (_arr(a) for a in (points, kernel_extent, omega, w, sigma_t, sigma_s, q))
+    _check_shapes(opt.dim, x, R, om, ww, st, ss, qq)
     ctx = _P()
     s = load_library().mlpg_create(ctypes.byref(opt), x.shape[0], _ptr(x), _ptr(R), om.shape[0], _ptr(om),
                                    _ptr(ww), _ptr(st), _ptr(ss), _ptr(qq), ctypes.byref(ctx))
@@ -168,6 +186,8 @@ def mlpg_set_inflow(ctx, face, psi_b):
 
 def mlpg_set_initial(ctx, psi0=None):
     a = None if psi0 is None else _arr(psi0)
+    if a is not None and a.size != _state_size(ctx):
+        raise ValueError(f"psi0 must hold n * m = {_state_size(ctx)} values, got {a.size}")
     _check(ctx, load_library().mlpg_set_initial(ctx, _ptr(a)))
 
 
@@ -212,6 +232,8 @@ def mlpg_get_state(ctx, n, m):
 
 def mlpg_set_state(ctx, psi):
     a = _arr(psi)
+    if a.size != _state_size(ctx):
+        raise ValueError(f"psi must hold n * m = {_state_size(ctx)} values, got {a.size}")
     _check(ctx, load_library().mlpg_set_state(ctx, _ptr(a)))
 
 

@@ -440,6 +440,7 @@ mlpg_status mlpg_get_volumes(const mlpg_ctx *cctx, double *out) {
     if (!ctx || !out) return MLPG_ERR_ARG;
     if (ctx->state < 1) return set_err(ctx, MLPG_ERR_STATE, "volumes need integrate");
     GUARD(ctx);
+    CU(ctx, cudaStreamSynchronize(ctx->stream));   // the library stream does not block with the legacy one
     CU(ctx, cudaMemcpy(out, ctx->V, ctx->n * sizeof(double), cudaMemcpyDeviceToHost));
     return MLPG_OK;
 }

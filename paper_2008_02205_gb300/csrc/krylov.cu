@@ -691,7 +691,7 @@ static mlpg_status ensure_step_buffers(mlpg_ctx *ctx) {
     MLPG_TRY(dalloc(ctx, &ctx->rhs32, N));
     MLPG_TRY(dalloc(ctx, &ctx->sol32, N));
     MLPG_TRY(dalloc(ctx, &ctx->bpsi32, N));
-    MLPG_TRY(dalloc(ctx, &ctx->nvec, 8 * ctx->n));
+    if (!ctx->nvec) MLPG_TRY(dalloc(ctx, &ctx->nvec, 8 * ctx->n));   // mlpg_scalar_flux may have made it
     ctx->red_cap = 4096;
     MLPG_TRY(dalloc(ctx, &ctx->red, ctx->red_cap));
     void *hp = nullptr;

@@ -91,3 +91,21 @@ def test_default_options(lib):
     assert (o.precision, o.inner_restart, o.mixed_restart, o.check_every) == (0, 20, 20, 3)
     assert (o.mixed_reorth, o.mixed_half_prec, o.rk_order) == (0, 1, 1)
     assert (o.inner_tol, o.outer_tol, o.mixed_inner_tol) == (1e-12, 1e-12, 1e-2)
+
+
+@pytest.mark.parametrize("bad", ["points_dim", "omega_cols", "extent", "weights", "sigma_t", "sigma_s", "q"])
+def test_binding_rejects_mismatched_arrays_before_the_library_reads_them(lib, bad):
+    # the C side reads n * dim, n, 3 m and m values from the pointers it is given:
+    # the binding checks every shape first (no device needed, nothing reaches C)
+    import numpy as np
+    import paper_2008_02205_gb300 as pkg
+    n, m = 16, 4
+    args = dict(points=np.zeros((n, 2)), kernel_extent=np.ones(n), omega=np.tile([1.0, 0, 0], (m, 1)),
+                w=np.ones(m), sigma_t=np.ones(n), sigma_s=np.zeros(n), q=np.ones(n))
+    short = {"points_dim": ("points", np.zeros((n, 3))), "omega_cols": ("omega", np.zeros((m, 2))),
+             "extent": ("kernel_extent", np.ones(n - 1)), "weights": ("w", np.ones(m + 1)),
+             "sigma_t": ("sigma_t", np.ones(n - 1)), "sigma_s": ("sigma_s", np.ones((n, 1))),
+             "q": ("q", np.ones(2 * n))}[bad]
+    args[short[0]] = short[1]
+    with pytest.raises(ValueError):
+        pkg.mlpg_create(pkg.mlpg_default_options(dim=2), **args)
