@@ -164,10 +164,13 @@ mlpg_status mlpg_step(mlpg_ctx *ctx, double dt);
  * The contexts must be distinct and must not share a stream (contexts created
  * with a NULL stream own one): otherwise MLPG_ERR_ARG before any step.
  * Returns MLPG_OK when every step succeeded, else the first failing status in
- * index order; each context's mlpg_last_error describes its own failure.  The
- * paper states the problem for one point set; batching independent problems
- * has no counterpart there. */
-mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count);
+ * index order; each context's mlpg_last_error describes its own failure.
+ * status[count] (may be NULL) receives every context's own status, so that a
+ * caller can retire the failed problems and keep the others (whose steps are
+ * done); on an argument error it is left unwritten.  The paper states the
+ * problem for one point set; batching independent problems has no counterpart
+ * there. */
+mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count, mlpg_status *status);
 
 /* Scalar flux: kind 0 = point values phi_i = sum_j V_j U_j(x_i) Phi_j
  * (Eq. flux-expansion), kind 1 = coefficients Phi_i.  out[n], host. */

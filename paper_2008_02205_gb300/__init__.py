@@ -83,7 +83,7 @@ def load_library(path: str = LIB_PATH):
         "mlpg_integrate": (i32, [_P]),
         "mlpg_assemble": (i32, [_P]),
         "mlpg_step": (i32, [_P, dbl]),
-        "mlpg_step_batch": (i32, [_P, _P, ctypes.c_int]),
+        "mlpg_step_batch": (i32, [_P, _P, ctypes.c_int, _P]),
         "mlpg_scalar_flux": (i32, [_P, _P, ctypes.c_int]),
         "mlpg_scalar_flux_dev": (i32, [_P, _P, ctypes.c_int]),
         "mlpg_get_state": (i32, [_P, _P]),
@@ -203,15 +203,23 @@ def mlpg_step(ctx, dt):
     _check(ctx, load_library().mlpg_step(ctx, dt))
 
 
-def mlpg_step_batch(ctxs, dts):
-    """One step of each context, run concurrently (distinct contexts and streams)."""
+def mlpg_step_batch(ctxs, dts, raise_on_error=True):
+    """One step of each context, run concurrently (distinct contexts and
+    streams).  Returns every context's own status (0 = done); a failure raises
+    MlpgError naming the failed contexts unless raise_on_error is False.  An
+    argument error of the whole call (no step taken) always raises."""
     k = len(ctxs)
     arr = (_P * max(k, 1))(*ctxs)
     d = _arr(np.broadcast_to(np.asarray(dts, dtype=np.float64), (k,)))
-    st = load_library().mlpg_step_batch(arr, _ptr(d), k)
-    if st != MLPG_OK:
-        msgs = [(load_library().mlpg_last_error(c) or b"").decode() for c in ctxs]
-        raise MlpgError(st, "; ".join(f"[{i}] {m}" for i, m in enumerate(msgs) if m))
+    unwritten = 1                                   # not a status value
+    out = (ctypes.c_int * max(k, 1))(*([unwritten] * max(k, 1)))
+    st = load_library().mlpg_step_batch(arr, _ptr(d), k, out)
+    each = [int(out[i]) for i in range(k)]
+    if st != MLPG_OK and (k == 0 or each[0] == unwritten):
+        raise MlpgError(st, "; ".join(m for m in (mlpg_last_error(c) for c in ctxs if c) if m) or "bad batch")
+    if st != MLPG_OK and raise_on_error:
+        raise MlpgError(st, "; ".join(f"[{i}] {mlpg_last_error(c)}" for i, (c, s) in enumerate(zip(ctxs, each)) if s))
+    return each
 
 
 def mlpg_scalar_flux(ctx, n, kind=0):

@@ -1,6 +1,7 @@
 // C ABI of the library (include/mlpg.h): argument checks, the call-order state
 // machine, host<->device copies, stage outputs and statistics.  Every entry
 // point returns a status; nothing throws across the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -333,7 +334,7 @@ mlpg_status mlpg_step(mlpg_ctx *ctx, double dt) {
     CATCH_ALL(ctx)
 }
 
-mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count) {
+mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count, mlpg_status *status) {
     if (!ctxs || !dt || count < 0) return MLPG_ERR_ARG;
     for (int i = 0; i < count; ++i) {
         if (!ctxs[i]) return MLPG_ERR_ARG;
@@ -353,6 +354,7 @@ mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count) 
     st[0] = mlpg_step(ctxs[0], dt[0]);
     for (int i = next; i < count; ++i) st[i] = mlpg_step(ctxs[i], dt[i]);
     for (auto &t : th) t.join();
+    if (status) std::copy(st.begin(), st.end(), status);
     for (int i = 0; i < count; ++i)
         if (st[i] != MLPG_OK) return st[i];
     return MLPG_OK;

@@ -8,8 +8,10 @@ resident on the device, and advances all admitted problems together: each
 iteration is one ``mlpg_step_batch`` call, which steps every context on its
 own stream so that their kernels overlap.  A problem leaves as soon as its
 last step is done (its memory and slot go to the next arrivals), with its
-latency measured from its arrival.  All compute goes through the C ABI; this
-module only schedules.
+latency measured from its arrival.  A problem that cannot be set up, or whose
+step fails (an iteration cap, say), leaves with its error and its memory
+freed; the others carry on, since the batched call reports each context's own
+status.  All compute goes through the C ABI; this module only schedules.
 """
 from __future__ import annotations
 
@@ -71,11 +73,19 @@ class LibraryBackend:
 
     def open(self, req: Request):
         tp = self.pkg.TransportProblem.from_problem(req.problem, **req.options)
-        tp.integrate().assemble()
+        try:
+            tp.integrate().assemble()
+        except Exception:
+            tp.close()
+            raise
         return tp
 
     def step(self, handles, dts):
-        self.pkg.mlpg_step_batch([h.ctx for h in handles], dts)
+        """One concurrent step of every handle; returns None or an error
+        message per handle."""
+        st = self.pkg.mlpg_step_batch([h.ctx for h in handles], dts, raise_on_error=False)
+        return [None if s == 0 else f"step failed (status {s}): {self.pkg.mlpg_last_error(h.ctx)}"
+                for s, h in zip(st, handles)]
 
     def flux(self, h):
         return h.scalar_flux()
@@ -86,7 +96,11 @@ class LibraryBackend:
 
 class Server:
     """FIFO admission under a device-memory budget and a slot limit; one
-    concurrent step of every admitted problem per iteration."""
+    concurrent step of every admitted problem per iteration.
+
+    A backend provides open(request) -> handle, step(handles, dts) -> None
+    (all done) or a per-handle list of None / error message, flux(handle) and
+    close(handle)."""
 
     def __init__(self, hbm_budget_bytes: int, max_active: int = 16, backend=None, clock=time.perf_counter,
                  estimate=estimate_bytes, sleep=time.sleep):
@@ -105,44 +119,70 @@ class Server:
         active = []          # [request, handle, bytes, steps done]
         used = 0
         t0 = self.clock()
-        while pending or active:
-            now = self.clock() - t0
-            while pending and pending[0].arrival <= now and len(active) < self.max_active:
-                req = pending[0]
-                need = self.estimate(req.problem, req.options.get("precision", 0) == 1)   # 1: mixed
-                if need > self.budget:      # can never fit: refuse it
-                    pending.pop(0)
+
+        def retire(a, error=None):
+            nonlocal used
+            res = results[id(a[0])]
+            if error is None:
+                res.flux = self.backend.flux(a[1])
+            else:
+                res.error = error
+            self.backend.close(a[1])
+            res.finished = self.clock() - t0
+            used -= a[2]
+
+        try:
+            while pending or active:
+                now = self.clock() - t0
+                while pending and pending[0].arrival <= now and len(active) < self.max_active:
+                    req = pending[0]
+                    need = self.estimate(req.problem, req.options.get("precision", 0) == 1)   # 1: mixed
                     res = results[id(req)]
-                    res.error = f"needs {need} bytes, budget {self.budget}"
-                    res.admitted = res.finished = now
+                    if need > self.budget:      # can never fit: refuse it
+                        pending.pop(0)
+                        res.error = f"needs {need} bytes, budget {self.budget}"
+                        res.admitted = res.finished = now
+                        continue
+                    if used + need > self.budget:
+                        break                   # wait for memory to free up (FIFO)
+                    pending.pop(0)
+                    res.admitted = self.clock() - t0
+                    try:
+                        handle = self.backend.open(req)
+                    except Exception as e:      # bad input, geometry, device memory: this request only
+                        res.error = f"open failed: {e}"
+                        res.finished = self.clock() - t0
+                        continue
+                    active.append([req, handle, need, 0])
+                    used += need
+                if not active:
+                    if pending:                 # idle until the next arrival
+                        wait = pending[0].arrival - (self.clock() - t0)
+                        if wait > 0:
+                            self.sleep(min(wait, 0.01))
                     continue
-                if used + need > self.budget:
-                    break                   # wait for memory to free up (FIFO)
-                pending.pop(0)
-                results[id(req)].admitted = self.clock() - t0
-                active.append([req, self.backend.open(req), need, 0])
-                used += need
-            if not active:
-                if pending:                 # idle until the next arrival
-                    wait = pending[0].arrival - (self.clock() - t0)
-                    if wait > 0:
-                        self.sleep(min(wait, 0.01))
-                continue
-            self.peak_active = max(self.peak_active, len(active))
-            self.backend.step([a[1] for a in active], [a[0].dt for a in active])
-            self.iterations += 1
-            keep = []
+                self.peak_active = max(self.peak_active, len(active))
+                errors = self.backend.step([a[1] for a in active], [a[0].dt for a in active])
+                if errors is None:
+                    errors = [None] * len(active)
+                self.iterations += 1
+                keep = []
+                for a, err in zip(active, errors):
+                    if err is not None:
+                        retire(a, err)
+                        continue
+                    a[3] += 1
+                    if a[3] >= a[0].steps:
+                        retire(a)
+                    else:
+                        keep.append(a)
+                active = keep
+        finally:                                # an escaping error still releases every context
             for a in active:
-                a[3] += 1
-                if a[3] >= a[0].steps:
-                    res = results[id(a[0])]
-                    res.flux = self.backend.flux(a[1])
+                try:
                     self.backend.close(a[1])
-                    res.finished = self.clock() - t0
-                    used -= a[2]
-                else:
-                    keep.append(a)
-            active = keep
+                except Exception:
+                    pass
         return [results[id(r)] for r in requests]
 
 

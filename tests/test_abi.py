@@ -45,8 +45,10 @@ def test_null_arguments_rejected_without_device(lib):
     lib.mlpg_create.restype = ctypes.c_int
     assert lib.mlpg_create(None, 0, None, None, 0, None, None, None, None, None, None) == -1
     lib.mlpg_step_batch.restype = ctypes.c_int
-    assert lib.mlpg_step_batch(None, None, 1) == -1
-    assert lib.mlpg_step_batch((ctypes.c_void_p * 1)(None), (ctypes.c_double * 1)(0.1), 1) == -1
+    assert lib.mlpg_step_batch(None, None, 1, None) == -1
+    st = (ctypes.c_int * 1)(12345)
+    assert lib.mlpg_step_batch((ctypes.c_void_p * 1)(None), (ctypes.c_double * 1)(0.1), 1, st) == -1
+    assert st[0] == 12345          # argument errors leave the per-context statuses unwritten
     lib.mlpg_last_error.restype = ctypes.c_char_p
     assert lib.mlpg_last_error(None) == b"null context"
 

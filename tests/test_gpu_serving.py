@@ -35,3 +35,30 @@ def test_served_results_equal_alone_results():
     assert server.peak_active >= 2
     lat = latency_percentiles(res)
     assert 0 < lat["p50"] <= lat["p99"]
+
+
+def test_failed_requests_leave_alone_and_the_rest_are_served():
+    """One request hits an iteration cap in its first step and one cannot be
+    created (a point outside the box): each fails with its own error, and the
+    two healthy problems stepped in the same batches equal their solo runs."""
+    good = mi.batched_2d(2, seed=4300, n_range=(64, 200), steps=3)
+    capped = mi.batched_2d(1, seed=4310, n_range=(64, 100), steps=3)[0]
+    outside = mi.batched_2d(1, seed=4320, n_range=(64, 100), steps=3)[0]
+    outside.x = outside.x.copy()
+    outside.x[0, 0] = 1.5
+    mixed = dict(precision=pkg.MLPG_MIXED, refine_tol=1e-12)
+    reqs = [Request(good[0], 3, good[0].dt, options=mixed),
+            Request(capped, 3, capped.dt, options=dict(max_inner=1, inner_restart=2)),
+            Request(outside, 3, outside.dt, options=mixed),
+            Request(good[1], 3, good[1].dt, options=mixed)]
+    alone = []
+    for p in good:
+        with pkg.TransportProblem.from_problem(p, **mixed) as tp:
+            tp.integrate().assemble()
+            alone.append(tp.run(p.dt, 3))
+    res = Server(hbm_budget_bytes=1 << 34, max_active=4).run(reqs)
+    assert res[1].flux is None and "status -7" in res[1].error
+    assert res[2].flux is None and res[2].error.startswith("open failed")
+    for r, a in zip((res[0], res[3]), alone):
+        assert r.error is None
+        assert np.linalg.norm(r.flux - a) / np.linalg.norm(a) < 1e-9

@@ -96,3 +96,74 @@ def test_idle_until_first_arrival():
     srv, be = _server(budget=10)
     res = srv.run(reqs)
     assert res[0].admitted >= 0.5 and res[0].flux[0] == 2
+
+
+class FailingBackend(FakeBackend):
+    """Fails to open problems of size `bad_open` and fails the step of
+    problems of size `bad_step` once they have taken `after` steps."""
+
+    def __init__(self, bad_open=None, bad_step=None, after=0):
+        super().__init__()
+        self.bad_open, self.bad_step, self.after = bad_open, bad_step, after
+        self.closed = []
+
+    def open(self, req):
+        if req.problem.size == self.bad_open:
+            raise RuntimeError("geometry")
+        return super().open(req)
+
+    def step(self, handles, dts):
+        errs = []
+        for h in handles:
+            if self.open_sizes[h] == self.bad_step and self.steps[h] >= self.after:
+                errs.append("not converged")
+            else:
+                errs.append(None)
+        self.calls.append((list(handles), sum(self.open_sizes[h] for h in handles)))
+        for h, e in zip(handles, errs):
+            if e is None:
+                self.steps[h] += 1
+        return errs
+
+    def close(self, h):
+        self.closed.append(h)
+        super().close(h)
+
+
+def _failing_server(budget, **kw):
+    clk, be = FakeClock(), FailingBackend(**kw)
+    return Server(budget, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size), be
+
+
+def test_a_request_that_cannot_be_opened_fails_alone():
+    reqs = [Request(FakeProblem(s), steps=3, dt=0.1) for s in (2, 7, 3)]
+    srv, be = _failing_server(10, bad_open=7)
+    res = srv.run(reqs)
+    assert "open failed" in res[1].error and res[1].flux is None
+    assert res[0].error is None and res[2].error is None
+    assert res[0].flux[0] == 3 and res[2].flux[0] == 3
+    assert max(used for _, used in be.calls) == 5      # the failed open charged no memory
+    assert not be.open_sizes                          # everything opened was closed
+
+
+def test_a_failing_step_retires_its_request_and_the_others_finish():
+    reqs = [Request(FakeProblem(s), steps=6, dt=0.1) for s in (2, 4, 3)]
+    srv, be = _failing_server(9, bad_step=4, after=2)
+    res = srv.run(reqs)
+    assert res[1].error == "not converged" and res[1].flux is None
+    assert res[0].flux[0] == 6 and res[2].flux[0] == 6
+    # the failed problem left after its third step call; the others went on without it
+    assert all(len(h) == 2 for h, _ in be.calls[3:]) and len(be.calls) == 6
+    assert not be.open_sizes
+
+
+def test_an_escaping_error_still_closes_every_context():
+    class Boom(FailingBackend):
+        def step(self, handles, dts):
+            raise ValueError("bad batch")
+    clk, be = FakeClock(), Boom()
+    srv = Server(10, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size)
+    import pytest
+    with pytest.raises(ValueError):
+        srv.run([Request(FakeProblem(1), steps=2, dt=0.1), Request(FakeProblem(2), steps=2, dt=0.1)])
+    assert len(be.closed) == 2 and not be.open_sizes
