@@ -186,6 +186,22 @@ def test_rectangle_ragged_rows():
     assert _rel(phi, ref) < 1e-9
 
 
+@pytest.mark.parametrize("precision,tol", [(pkg.MLPG_FP64, 1e-9), (pkg.MLPG_MIXED, 1e-8)])
+def test_line_source_and_absorbing_disk_on_a_centred_box(precision, tol):
+    """The scaled-down asteroid problem (Sec. 5.4, App. B): box [-1, 1]^2, a disk
+    with sigma_t = 10 in a 0.5 background, no scattering, a Gaussian source,
+    one steady step with 32 azimuths x 2 mu-weighted polar levels (64
+    ordinates).  The box comes from the problem (negative lower corner)."""
+    prob = mi.asteroid_2d(n_per_dim=20, n_azimuth=32, n_polar=2)
+    ref, *_ = _oracle_run(prob)
+    with pkg.TransportProblem.from_problem(prob, precision=precision, inner_tol=1e-13, outer_tol=1e-13,
+                                           refine_tol=1e-12) as tp:
+        tp.integrate().assemble()
+        assert np.allclose(tp.volumes().sum(), 4.0, rtol=1e-12)
+        phi = tp.run(prob.dt, prob.steps)
+    assert _rel(phi, ref) < tol
+
+
 def test_initial_state_and_restart(small):
     prob, disc, F, _ = small
     rng = np.random.default_rng(3)
