@@ -18,6 +18,7 @@ Sec. 4.1).
 """
 from __future__ import annotations
 
+import functools
 import itertools
 import math
 from dataclasses import dataclass, field
@@ -108,12 +109,19 @@ def _next_moment_residual(order: int, mu1: float):
 
 def level_symmetric(order: int, dim: int):
     """Level-symmetric S_N set: (omega[M, 3], w[M]) with sum(w) = 4*pi.
+    Built once per (order, dim); every call returns fresh copies.
 
     mu1 is the root, in (0, 1/sqrt(3)), of the first even moment not used for
     the weights, taken among roots with all class weights positive (the root
     with the largest mu1 when several exist).  3D: N(N+2) directions; 2D: the
     N(N+2)/2 directions with Omega_z > 0, weights doubled.
     """
+    om, w = _level_symmetric_cached(int(order), int(dim))
+    return om.copy(), w.copy()
+
+
+@functools.lru_cache(maxsize=None)
+def _level_symmetric_cached(order: int, dim: int):
     if order < 2 or order % 2:
         raise ValueError("S_N order must be even and >= 2")
     n = order // 2
@@ -405,3 +413,56 @@ def asteroid_2d(n_per_dim: int = 32, n_azimuth: int = 64, n_polar: int = 2,
     return Problem(name=f"2d-asteroid-{n_per_dim}x{n_per_dim}-A{n_azimuth}P{n_polar}", dim=2, x=x,
                    R=np.full(len(x), 2.0 * h), omega=omega, w=w, sigma_t=st, sigma_s=np.zeros(len(x)),
                    q=q, dt=math.inf, steps=1, lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), spacing=h)
+
+
+# ---------------------------------------------------------------------------
+# request stream of the serving configuration
+# ---------------------------------------------------------------------------
+def serving_stream(count: int = 64, rate: float = 2.0, seed: int = 5000, n_range=(4096, 250000),
+                   p3d: float = 0.25, sn_2d=(4, 6, 8, 10, 12), sn_3d=(4, 8, 12), p_refined: float = 0.25,
+                   steps_range=(5, 50), dt: float = 0.01):
+    """Arriving transport problems: a list of (Problem, arrival time).
+
+    Arrivals are a Poisson process of the given rate (exponential gaps, the
+    first one after a gap from time 0).  Per request, drawn from numpy
+    PCG64(seed): dimension 3 with probability p3d, else 2; a point count
+    log-uniform in n_range, rounded to a k^dim lattice; in 2D S_N from sn_2d
+    (12 to 84 directions), in 3D the selectively refined set of Alg. 2 within
+    15 degrees of +x (272 directions) with probability p_refined, else S_N from
+    sn_3d (24 to 168); two regions, the centred box [0.4, 0.6]^dim and the
+    rest, each with sigma_t log-uniform in [0.1, 100]; one scattering ratio
+    uniform in [0, 0.99]; q = 1 for x_0 < 0.5; vacuum boundaries; steps
+    uniform in steps_range (inclusive); backward-Euler step dt.  Problem b uses
+    lattice seed seed + 1 + b."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    t = 0.0
+    refined_set = None
+    for b in range(count):
+        t += rng.exponential(1.0 / rate)
+        dim = 3 if rng.uniform() < p3d else 2
+        npts = math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))
+        k = max(2, int(round(npts ** (1.0 / dim))))
+        refined = dim == 3 and rng.uniform() < p_refined
+        sn = int(rng.choice(np.asarray(sn_2d if dim == 2 else sn_3d)))
+        s_in, s_out = np.exp(rng.uniform(math.log(0.1), math.log(100.0), 2))
+        ratio = float(rng.uniform(0.0, 0.99))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+
+        def st(x, r, s_in=s_in, s_out=s_out):
+            inside = np.all((x >= 0.4) & (x <= 0.6), axis=1)
+            return np.where(inside, s_in, s_out)
+
+        def ss(x, r, sig_t, ratio=ratio):
+            return ratio * sig_t
+
+        def qq(x, r):
+            return np.where(x[:, 0] < 0.5, 1.0, 0.0)
+        p = make_problem(f"serve{b}-{dim}d-{k}^{dim}", k, dim, sn, seed + 1 + b, st, ss, qq, dt, steps)
+        if refined:
+            if refined_set is None:
+                refined_set = refined_quadrature(1, 5, cone_hits((1.0, 0.0, 0.0), 15.0))
+            p.omega, p.w = refined_set[0].copy(), refined_set[1].copy()
+            p.name += "-refined"
+        out.append((p, t))
+    return out

@@ -167,3 +167,28 @@ def test_an_escaping_error_still_closes_every_context():
     with pytest.raises(ValueError):
         srv.run([Request(FakeProblem(1), steps=2, dt=0.1), Request(FakeProblem(2), steps=2, dt=0.1)])
     assert len(be.closed) == 2 and not be.open_sizes
+
+
+def test_serves_a_poisson_stream_under_the_estimated_budget():
+    import mlpg_inputs as mi
+    from paper_2008_02205_gb300.serving import estimate_bytes
+
+    class SizedBackend(FakeBackend):
+        def open(self, req):
+            h = id(req)
+            self.open_sizes[h] = estimate_bytes(req.problem, True)
+            self.steps[h] = 0
+            return h
+
+    stream = mi.serving_stream(count=30, rate=50.0, seed=5200, n_range=(64, 2048))
+    reqs = [Request(p, p.steps, p.dt, arrival=t, options={"precision": 1}) for p, t in stream]
+    est = [estimate_bytes(p, True) for p, _ in stream]
+    budget = 3 * max(est)
+    clk, be = FakeClock(), SizedBackend()
+    srv = Server(budget, max_active=8, backend=be, clock=clk, sleep=clk.sleep)
+    res = srv.run(reqs)
+    assert all(r.error is None and r.flux[0] == r.request.steps for r in res)
+    assert max(used for _, used in be.calls) <= budget
+    assert srv.peak_active >= 2
+    admitted = [r.admitted for r in sorted(res, key=lambda r: r.request.arrival)]
+    assert admitted == sorted(admitted)
