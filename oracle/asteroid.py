@@ -25,7 +25,8 @@ from scipy.special import exp1
 
 
 def disk_chord(x_src, x_eval, centre, radius):
-    """Length of the segment x_src -> x_eval (x_eval [k, 2]) inside the disk.
+    """Length of the segment x_src -> x_eval (x_eval [k, 2]) inside the disk
+    (App. B, Eq. parametric-s and Eq. s-intercept).
 
     With x = x_src + (x_eval - x_src) s and the disk moved to the origin,
     |x|^2 = radius^2 is l2 s^2 + 2 l1 s + l0 = 0 with l0 = |x_src|^2 - radius^2,
@@ -81,7 +82,7 @@ def scalar_flux_polar(omega, r, mu, a):
 
 def superposed_scalar_flux(x_eval, sources, strengths, centre, radius, sigma_background,
                            sigma_asteroid, mu=None, a=None):
-    """sum_j S_j phi(x_eval; source j) for line sources at `sources` [J, 2] with
+    """(App. B, by superposition) sum_j S_j phi(x_eval; source j) for line sources at `sources` [J, 2] with
     strengths S_j; the polar integral is exact (E2) unless (mu, a) are given.
     Undefined (inf) at a source point."""
     xe = np.atleast_2d(np.asarray(x_eval, np.float64))

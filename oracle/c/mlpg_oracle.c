@@ -50,7 +50,7 @@
 #define LABEL_EXTENT (-100)
 
 /* ======================================================================
- * A. Reference quadrature rules
+ * A. Reference quadrature rules (Sec. 3.2 and Sec. 5; mapped onto the cells as in App. A)
  * ====================================================================== */
 
 /* Eigen-decomposition of a small dense symmetric matrix a[n*n] by cyclic
@@ -94,7 +94,7 @@ static void sym_eig_jacobi(int n, double *a, double *v)
     }
 }
 
-/* Gauss-Jacobi rule on [-1, 1] for the weight (1 - t)^a (1 + t)^b, n points,
+/* (Sec. 3.2, App. A) Gauss-Jacobi rule on [-1, 1] for the weight (1 - t)^a (1 + t)^b, n points,
  * by Golub-Welsch: nodes are the eigenvalues of the symmetric tridiagonal
  * matrix of the Jacobi three-term recurrence, weights mu0 * (v_0k)^2.
  * Nodes returned in increasing order. */
@@ -133,7 +133,7 @@ int orc_gauss_jacobi(int n, double a, double b, double *t, double *wt)
     return ORC_OK;
 }
 
-/* Reference triangle {xi1, xi2 >= 0, xi1 + xi2 <= 1}: conical product of an
+/* (Sec. 3.2, Sec. 5.1) Reference triangle {xi1, xi2 >= 0, xi1 + xi2 <= 1}: conical product of an
  * n-point Gauss-Jacobi(1,0) rule in u and an n-point Gauss-Legendre rule in v,
  * xi1 = u, xi2 = (1 - u) v, exact for total degree 2n - 1.  Point k = iu*n + iv.
  * xi[2*k], w[k]; sum(w) = 1/2. */
@@ -156,7 +156,7 @@ int orc_triangle_rule(int n, double *xi, double *w)
 /* Gauss-Legendre on [-1, 1] (App. A line map x = p0 + (p1 - p0)(xi + 1)/2). */
 int orc_line_rule(int n, double *t, double *w) { return orc_gauss_jacobi(n, 0.0, 0.0, t, w); }
 
-/* Reference tetrahedron {xi >= 0, xi1 + xi2 + xi3 <= 1}: conical product of
+/* (Sec. 3.2, Sec. 5) Reference tetrahedron {xi >= 0, xi1 + xi2 + xi3 <= 1}: conical product of
  * n-point Gauss-Jacobi(2,0) in u, Gauss-Jacobi(1,0) in v and Gauss-Legendre in
  * s, xi1 = u, xi2 = (1 - u) v, xi3 = (1 - u)(1 - v) s (Jacobian
  * (1 - u)^2 (1 - v), carried by the Jacobi weights), exact for total degree
@@ -192,6 +192,7 @@ static double dist(int dim, const double *a, const double *b)
     return sqrt(s);
 }
 
+/* (Sec. 3.4) Overlap rows of all points, columns sorted; see section B. */
 int64_t orc_neighbors(int dim, int64_t n, const double *x, const double *R, int64_t *rowptr,
                       int32_t *col)
 {
@@ -247,7 +248,7 @@ static int clip_polygon(int nv, double *vx, double *vy, int32_t *lab, double *wx
     return out;
 }
 
-/* Cells of all points.  cptr[n+1]; verts[2*cap]; labels[cap]; vol[n].
+/* (Sec. 3.1, Fig. 1) Cells of all points.  cptr[n+1]; verts[2*cap]; labels[cap]; vol[n].
  * Pass verts == NULL to get the vertex counts only.  Returns total vertices. */
 int64_t orc_cells_2d(int64_t n, const double *x, const double *R, const double *lo,
                      const double *hi, const int64_t *rowptr, const int32_t *col, int64_t *cptr,
@@ -338,6 +339,8 @@ int64_t orc_volume_qps_2d(int64_t n, const double *x, const int64_t *cptr, const
     return c;
 }
 
+/* (Sec. 3.2, App. A) Boundary points: the Gauss-Legendre rule on every cell edge that
+ * lies on the domain boundary, with the edge's face index; see section D. */
 int64_t orc_boundary_qps_2d(int64_t n, const int64_t *cptr, const double *verts,
                             const int32_t *labels, int nref, double *xb, double *wb, int32_t *face,
                             int32_t *owner)
@@ -450,7 +453,7 @@ static double poly3_rmax(const poly3 *P, const double *g)
     return sqrt(r2);
 }
 
-/* Clip P by the bisector of (xi, xj) into W, then copy back.  cut[] holds up
+/* (Sec. 3.1) Clip P by the bisector of (xi, xj) into W, then copy back.  cut[] holds up
  * to 2 cap_v cap_f points.  tol: length scale of "the same point".  Returns 0,
  * or ORC_ERR_CAP when a capacity is exceeded. */
 static int poly3_clip(poly3 *P, poly3 *W, double *cut, const double *xi, const double *xj, int32_t j,
@@ -576,7 +579,7 @@ static double poly3_volume(const poly3 *P, const double *g)
     return vol;
 }
 
-/* Cells of all points.  fptr[n+1] (faces of each cell), vol[n], *nfaces = all
+/* (Sec. 3.1) Cells of all points.  fptr[n+1] (faces of each cell), vol[n], *nfaces = all
  * faces; with vptr/verts/labels NULL only the counts are produced.  Otherwise
  * vptr[nfaces+1] (vertices of each face), verts[3 * total], labels[nfaces].
  * Returns the total number of face vertices, or a negative error. */
@@ -720,6 +723,7 @@ static double kernel_w(double chi)
     if (chi < 2.0) return 0.25 * (2.0 - chi) * (2.0 - chi) * (2.0 - chi);
     return 0.0;
 }
+/* (Sec. 2.1) derivative of the cubic spline in chi */
 static double kernel_dw(double chi)
 {
     if (chi < 1.0) return -3.0 * chi + 2.25 * chi * chi;
@@ -776,7 +780,8 @@ static int rk_basis(int dim, int order, const double *xi, double *P, double dP[3
     return k;
 }
 
-/* RK functions at the point xe from the candidate list cand[ncand].
+/* (Sec. 2.2, Eq. rk-matrix and its gradient) RK functions at the point xe from
+ * the candidate list cand[ncand].
  * Supported j: |xe - x_j| < R_j.  Writes idx[ns], U[ns], dU[ns*dim]; returns
  * ns, or ORC_ERR_SINGULAR if the moment matrix cannot be inverted.
  *   M = sum_j V_j W_j P_j P_j^T,   C = M^{-1} e_1
@@ -854,7 +859,7 @@ static int rk_eval(int dim, int order, const double *xe, double s, int ncand, co
     return ns;
 }
 
-/* RK functions at npts points; the candidates of point p are the overlap row of
+/* (Sec. 2.2) RK functions at npts points; the candidates of point p are the overlap row of
  * owner[p] and the basis scale is h_owner = R_owner / 2.  CSR output: sptr[npts+1],
  * sidx, U, dU[*dim].  Pass sidx == NULL to count only.  Returns total entries or
  * a negative error. */
@@ -909,6 +914,7 @@ static int64_t find_pos(const int64_t *rowptr, const int32_t *col, int32_t a, in
     return -1;
 }
 
+/* (Sec. 4.1) numbers of integrated matrices and vectors; layout in section F */
 int orc_n_mats(int dim) { return 3 + 3 * dim + dim * dim + 2 * dim; }
 int orc_n_vecs(int dim) { return 1 + dim + 2 * dim; }
 

@@ -262,7 +262,7 @@ def rk_at_points(x, R, V, rowptr, col, pts, owner, order=1):
 
 
 def face_normals(dim):
-    """Outward normals of the box faces, order -x, +x, -y, +y (, -z, +z)."""
+    """Outward normals of the box faces (Sec. 4.1 boundary terms), order -x, +x, -y, +y (, -z, +z)."""
     nf = np.zeros((2 * dim, 3))
     for a in range(dim):
         nf[2 * a, a] = -1.0
@@ -303,7 +303,7 @@ class Discretization:
 
     # -- integration (Alg. 1) ---------------------------------------------
     def assemble(self, sigma_t_q, sigma_s_q, q_q):
-        """Integrate all forms with material values given per volume qp."""
+        """Integrate all forms (Alg. 1, Sec. 4.1) with material values given per volume qp."""
         d, n, nnz = self.dim, self.n, self.nnz
         L = lib()
         nm, nv = L.orc_n_mats(d), L.orc_n_vecs(d)
@@ -332,7 +332,7 @@ class Discretization:
         return F
 
     def assemble_per_point(self, sigma_t, sigma_s, q):
-        """Materials constant over each point's cell (value of the owner point)."""
+        """Alg. 1 with materials constant over each point's cell (value of the owner point)."""
         o = self.vq.owner
         return self.assemble(np.asarray(sigma_t)[o], np.asarray(sigma_s)[o], np.asarray(q)[o])
 
@@ -420,7 +420,7 @@ class Transport:
             self._kappa = kappa
 
     def Linv(self, rhs):
-        """Block-diagonal-in-angle inverse; rhs[M, n]."""
+        """L^{-1}, block-diagonal in angle (Sec. 4.2); rhs[M, n]."""
         return np.stack([self._lu[m].solve(rhs[m]) for m in range(self.M)])
 
     def D(self, Psi):
@@ -453,7 +453,7 @@ class Transport:
 
 
 def gmres(apply, b, x0, tol, restart, maxit, precond=None):
-    """Restarted GMRES (modified Gram-Schmidt Arnoldi, Givens rotations),
+    """Restarted GMRES (the Krylov solver of Sec. 4.2; modified Gram-Schmidt Arnoldi, Givens rotations),
     right preconditioned by `precond` when given.  Stops when
     ||b - A x|| <= tol * ||b||.  Returns (x, iterations, relative residual)."""
     x = np.array(x0, dtype=np.float64, copy=True)
@@ -590,7 +590,7 @@ class Solver:
         return Psi, Phi, StepStats(its, res)
 
     def step_direct(self, Psi_prev, dt):
-        """The same step from one sparse LU of the coupled system
+        """(Sec. 4.2) The same step from one sparse LU of the coupled system
         (L - MS D) Psi = T Psi^{n-1} + r (unknowns ordered direction-major)."""
         tr = self.tr
         kappa = 0.0 if not np.isfinite(dt) else 1.0 / (tr.c * dt)
@@ -605,7 +605,7 @@ class Solver:
         return Psi, tr.D(Psi)
 
     def run(self, Psi0, dt, steps, direct=False, src=None):
-        """Time loop from Psi0.  src(n) -> [M, n] extra source of step n (1-based)."""
+        """Backward-Euler time loop (Sec. 4.1) from Psi0.  src(n) -> [M, n] extra source of step n (1-based)."""
         Psi = np.array(Psi0, dtype=np.float64, copy=True)
         Phi = self.tr.D(Psi)
         stats = []
@@ -623,7 +623,7 @@ class Solver:
 # whole-problem convenience
 # ---------------------------------------------------------------------------
 def solve_problem(prob, steps=None, direct=False, outer_tol=1e-13, inner="lu", return_all=False):
-    """Run a mlpg_inputs.Problem (per-point materials) for `steps` steps from
+    """(Sec. 4.1-4.2, Eq. flux-expansion for the output) Run a mlpg_inputs.Problem (per-point materials) for `steps` steps from
     Psi = 0 and return the point values phi_i of the scalar flux."""
     disc = Discretization(prob.x, prob.R, prob.lo, prob.hi)
     F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
