@@ -9,7 +9,8 @@
  * MLPG_ERR_STATE.  No call aborts or throws: each returns a status and, on
  * failure, mlpg_last_error() describes it.  Inputs are copied at create; the
  * caller keeps ownership of every pointer it passes.  Host-pointer variants
- * copy through pinned staging on the library stream; `_dev` variants take
+ * copy directly from or to the caller's (pageable or pinned) memory on the
+ * library stream and return once the copy is complete; `_dev` variants take
  * device pointers valid on the device that was current at create.
  *
  * All arrays are row-major.  Angular fluxes use the layout psi[i][m] (point i,
@@ -98,7 +99,8 @@ typedef struct {
     int64_t kernel_launches;     /* kernels this context launched since create */
 } mlpg_stats;
 
-/* Default options (values listed in mlpg_options). */
+/* Default options (values listed in mlpg_options); a NULL opt is ignored.  A
+ * library service with no paper counterpart. */
 void mlpg_default_options(mlpg_options *opt);
 
 /* Create a problem (Sec. 4.1, Eq. transport-equation with the discrete
@@ -120,7 +122,8 @@ mlpg_status mlpg_create(const mlpg_options *opt, int64_t n, const double *points
                         const double *w, const double *sigma_t, const double *sigma_s,
                         const double *q, mlpg_ctx **out);
 
-/* Same as mlpg_create with every array a device pointer. */
+/* Same as mlpg_create with every array a device pointer (readable from the
+ * device current at this call); the same checks, errors and *out contract. */
 mlpg_status mlpg_create_dev(const mlpg_options *opt, int64_t n, const double *points,
                             const double *kernel_extent, int32_t m, const double *omega,
                             const double *w, const double *sigma_t, const double *sigma_s,
@@ -128,11 +131,14 @@ mlpg_status mlpg_create_dev(const mlpg_options *opt, int64_t n, const double *po
 
 /* Incoming isotropic angular flux psi_b on box face `face` (0:-x 1:+x 2:-y
  * 3:+y, in 3D also 4:-z 5:+z), Eq. rad-boundary.  Default 0 (vacuum).  Any
- * state after create. */
+ * state after create; takes effect at the next step.  MLPG_ERR_ARG for a face
+ * outside [0, 2 dim) or a non-finite psi_b. */
 mlpg_status mlpg_set_inflow(mlpg_ctx *ctx, int face, double psi_b);
 
 /* Initial angular flux coefficients Psi_i(0) = psi_init(x_i) (Sec. 4.1), host
- * psi0[n*m] in [i][m] layout; NULL = 0.  Any state after create. */
+ * psi0[n*m] in [i][m] layout (the caller guarantees n*m values); NULL = 0.
+ * Any state after create.  Also clears the step history the mixed-precision
+ * predictor extrapolates from. */
 mlpg_status mlpg_set_initial(mlpg_ctx *ctx, const double *psi0);
 
 /* Neighbour search (Sec. 3.4, overlap connectivity), Voronoi-like cells and
@@ -144,7 +150,10 @@ mlpg_status mlpg_set_initial(mlpg_ctx *ctx, const double *psi0);
 mlpg_status mlpg_integrate(mlpg_ctx *ctx);
 
 /* Quadrature-outermost integration of every bilinear / linear form of the
- * SUPG weak transport equation (Alg. 1, Eq. weak-transport). */
+ * SUPG weak transport equation (Alg. 1, Eq. weak-transport).  MLPG_ERR_STATE
+ * unless integrated; MLPG_ERR_RK_SINGULAR, MLPG_ERR_ARG (too many functions
+ * reach one element) or MLPG_ERR_GEOMETRY (a supported pair outside the overlap
+ * pattern) from the device checks. */
 mlpg_status mlpg_assemble(mlpg_ctx *ctx);
 
 /* One backward-Euler step (Sec. 4.1) solved as in Sec. 4.2: first-flight
@@ -173,20 +182,30 @@ mlpg_status mlpg_step(mlpg_ctx *ctx, double dt);
 mlpg_status mlpg_step_batch(mlpg_ctx *const *ctxs, const double *dt, int count, mlpg_status *status);
 
 /* Scalar flux: kind 0 = point values phi_i = sum_j V_j U_j(x_i) Phi_j
- * (Eq. flux-expansion), kind 1 = coefficients Phi_i.  out[n], host. */
+ * (Eq. flux-expansion), kind 1 = coefficients Phi_i.  out[n], host; returns
+ * when out is written.  MLPG_ERR_STATE before integrate, MLPG_ERR_ARG for
+ * another kind. */
 mlpg_status mlpg_scalar_flux(mlpg_ctx *ctx, double *out, int kind);
 
-/* Same with a device pointer; ordered on the library stream. */
+/* Same with a device pointer out[n]; the work is queued on the library stream
+ * and the call returns without waiting (synchronise that stream before
+ * reading out). */
 mlpg_status mlpg_scalar_flux_dev(mlpg_ctx *ctx, double *out, int kind);
 
-/* Angular flux coefficients Psi[n*m] ([i][m] layout), host; and restore. */
+/* Angular flux coefficients Psi[n*m] ([i][m] layout), host: the state of the
+ * time-dependent problem (Sec. 4.1), read back and restored for checkpoints
+ * (a library service; the paper has no restart).  mlpg_set_state is
+ * mlpg_set_initial with a non-NULL psi. */
 mlpg_status mlpg_get_state(const mlpg_ctx *ctx, double *psi);
 mlpg_status mlpg_set_state(mlpg_ctx *ctx, const double *psi);
 
+/* Counters of this context (mlpg_stats); the iteration counts are those of
+ * Sec. 5.3's outer and inner solves.  MLPG_ERR_ARG for NULL arguments. */
 mlpg_status mlpg_get_stats(const mlpg_ctx *ctx, mlpg_stats *stats);
 
 /* Enable device timing of the batched L-apply launches (CUDA events on the
- * library stream); the totals appear in mlpg_stats.spmm_ms. */
+ * library stream); the totals appear in mlpg_stats.spmm_ms.  A measurement
+ * service with no paper counterpart. */
 mlpg_status mlpg_enable_timing(mlpg_ctx *ctx, int on);
 
 /* ---- stage outputs, for inspection and parity checks -------------------- */
@@ -197,21 +216,26 @@ mlpg_status mlpg_get_neighbors(const mlpg_ctx *ctx, int64_t *rowptr, int32_t *co
 /* Cell volumes V_i (Sec. 3.1), host out[n]. */
 mlpg_status mlpg_get_volumes(const mlpg_ctx *ctx, double *out);
 
-/* Number of integrated matrices / vectors and their values in this order:
+/* The integrated forms of Eq. weak-transport (Sec. 4.1, Alg. 1).  Number of
+ * integrated matrices / vectors and their values in this order:
  *   matrices (nnz each): M0, Mt, Ms, G^a (dim), Gt^a (dim), Gs^a (dim),
  *                        K^ab (dim*dim, a-major), S_f (2*dim)
  *   vectors (n each):    Q0, Q^a (dim), B_f (2*dim)
  * with test function U_i (row) and trial function V_j U_j (column):
  *   M0 <U_i,V_jU_j>, Mt/Ms with sigma_t/sigma_s, G^a <d_a U_i, V_jU_j>,
  *   K^ab <d_a U_i, d_b V_jU_j>, S_f (U_i, V_jU_j) on face f, Q0 <U_i,q>,
- *   Q^a <d_a U_i, q>, B_f (U_i, 1) on face f.  Host out arrays. */
+ *   Q^a <d_a U_i, q>, B_f (U_i, 1) on face f.  Host out arrays
+ * mats[n_matrices * nnz], vecs[n_vectors * n].  MLPG_ERR_STATE before
+ * assemble. */
 int mlpg_n_matrices(int dim);
 int mlpg_n_vectors(int dim);
 mlpg_status mlpg_get_forms(const mlpg_ctx *ctx, double *mats, double *vecs);
 
 /* Batched transport operator (Sec. 4.2, operator L): Y[i][m] = (L_m X_m)_i
  * for all directions at once, for the 1/(c dt) of `dt`; X, Y device [n][m]
- * arrays of `precision` (MLPG_FP64: double, MLPG_MIXED: float). */
+ * arrays of `precision` (MLPG_FP64: double, MLPG_MIXED: float), queued on the
+ * library stream.  MLPG_ERR_STATE before assemble, MLPG_ERR_ARG for another
+ * precision or dt <= 0. */
 mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void *X, void *Y);
 
 /* ---- allocation-free helper ----------------------------------------------- */
@@ -244,9 +268,13 @@ mlpg_status mlpg_overlap_counts_noalloc(int dim, int64_t n, const double *points
                                         const double *kernel_extent, const double *lo,
                                         const double *hi, int32_t *counts, void *stream);
 
-/* Last error message of this context ("" when none). */
+/* Last error message of this context ("" when none; "null context" for NULL).
+ * Valid until the next call on the context. */
 const char *mlpg_last_error(const mlpg_ctx *ctx);
 
+/* Waits for the context's stream, frees every device and pinned allocation and
+ * the stream it owns (not a caller's stream); NULL is accepted.  The pointer
+ * is invalid afterwards. */
 void mlpg_destroy(mlpg_ctx *ctx);
 
 #ifdef __cplusplus
