@@ -52,6 +52,24 @@ def _args():
     return ap.parse_args()
 
 
+def _max_over_ranks(x, world, device=None):
+    """The largest x over all ranks (a job takes as long as its slowest rank);
+    x itself when there is one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(world, solves_per_rank, seconds):
+    """Whole-job solves/s: every rank solved solves_per_rank problems of its own
+    (weak scaling) in `seconds`, the slowest rank's time."""
+    return world * solves_per_rank / seconds
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -315,12 +333,8 @@ def main():
         spmm_launch += stats["spmm_launches"]
         launches += stats["kernel_launches"]
     clk = clocks.stop()
-    tot_ms = sum(per)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps / (tot_ms / 1e3)
+    tot_ms = _max_over_ranks(sum(per), world, dev)
+    value = _job_rate(world, args.steps, tot_ms / 1e3)
     # end to end through the host-pointer API (copies inside the timed region)
     e2e_times = []
     for _ in range(0 if args.no_e2e else max(1, args.steps)):
@@ -329,7 +343,7 @@ def main():
         phi_host = solve_host()
         e2e_times.append(time.perf_counter() - t0)
     h2d = sum(v.nbytes for v in host.values())
-    e2e_value = world / statistics.mean(e2e_times) if e2e_times else None
+    e2e_value = _job_rate(world, 1, _max_over_ranks(statistics.mean(e2e_times), world, dev)) if e2e_times else None
     # FP64 comparison solve (the plain FP64 GPU path) and error of this precision vs it
     fp64_info = None
     if not args.no_fp64_compare and prec == pkg.MLPG_MIXED:
