@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libmlpg.so")
 MLPG_OK = 0
 STATUS = {0: "MLPG_OK", -1: "MLPG_ERR_ARG", -2: "MLPG_ERR_STATE", -3: "MLPG_ERR_OOM", -4: "MLPG_ERR_CUDA",
           -5: "MLPG_ERR_GEOMETRY", -6: "MLPG_ERR_RK_SINGULAR", -7: "MLPG_ERR_NOT_CONVERGED"}
+(MLPG_ERR_ARG, MLPG_ERR_STATE, MLPG_ERR_OOM, MLPG_ERR_CUDA, MLPG_ERR_GEOMETRY, MLPG_ERR_RK_SINGULAR,
+ MLPG_ERR_NOT_CONVERGED) = range(-1, -8, -1)
 MLPG_FP64 = 0
 MLPG_MIXED = 1
 

@@ -111,3 +111,48 @@ def test_binding_rejects_mismatched_arrays_before_the_library_reads_them(lib, ba
     args[short[0]] = short[1]
     with pytest.raises(ValueError):
         pkg.mlpg_create(pkg.mlpg_default_options(dim=2), **args)
+
+
+@pytest.mark.parametrize("field,value", [("dim", 4), ("dim", 1), ("rk_order", 3), ("rk_order", -1),
+                                         ("mixed_reorth", 2), ("mixed_half_prec", 2), ("outer_method", 2),
+                                         ("inner_restart", 0), ("inner_restart", 33), ("outer_restart", 33),
+                                         ("mixed_restart", 0), ("check_every", 0), ("c", 0.0), ("c", -1.0),
+                                         ("tau_factor", -0.5), ("precision", 5)])
+def test_invalid_options_are_rejected_before_any_device_call(lib, field, value):
+    # option and size checks run before the library touches CUDA: *out stays NULL
+    import numpy as np
+    import paper_2008_02205_gb300 as pkg
+    o = pkg.mlpg_default_options()
+    setattr(o, field, value)
+    n, m = 16, 4
+    arr = [np.zeros((n, 2)), np.ones(n), np.tile([1.0, 0.0, 0.0], (m, 1)), np.ones(m), np.ones(n), np.zeros(n),
+           np.ones(n)]
+    ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arr]
+    out = ctypes.c_void_p()
+    L = pkg.load_library()
+    st = L.mlpg_create(ctypes.byref(o), n, ptrs[0], ptrs[1], m, ptrs[2], ptrs[3], ptrs[4], ptrs[5], ptrs[6],
+                       ctypes.byref(out))
+    assert st == pkg.MLPG_ERR_ARG and not out.value
+
+
+def test_empty_box_and_tiny_problems_are_rejected(lib):
+    import numpy as np
+    import paper_2008_02205_gb300 as pkg
+    L = pkg.load_library()
+    for n, lohi in ((16, ((0.0, 0.0), (1.0, 0.0))), (3, ((0.0, 0.0), (1.0, 1.0)))):
+        o = pkg.mlpg_default_options(lo=lohi[0], hi=lohi[1])
+        arr = [np.zeros((n, 2)), np.ones(n), np.array([[1.0, 0.0, 0.0]]), np.ones(1), np.ones(n), np.zeros(n),
+               np.ones(n)]
+        ptrs = [a.ctypes.data_as(ctypes.c_void_p) for a in arr]
+        out = ctypes.c_void_p()
+        st = L.mlpg_create(ctypes.byref(o), n, ptrs[0], ptrs[1], 1, ptrs[2], ptrs[3], ptrs[4], ptrs[5], ptrs[6],
+                           ctypes.byref(out))
+        assert st == pkg.MLPG_ERR_ARG and not out.value
+
+
+def test_binding_status_codes_match_the_header():
+    import paper_2008_02205_gb300 as pkg
+    txt = open(HEADER).read()
+    for name, val in re.findall(r"\b(MLPG_(?:OK|ERR_[A-Z_]+))\s*=\s*(-?\d+)", txt):
+        assert getattr(pkg, name) == int(val), name
+        assert pkg.STATUS[int(val)] == name
