@@ -323,8 +323,9 @@ class TransportProblem:
     @classmethod
     def from_problem(cls, prob, **options):
         """From an ``mlpg_inputs.Problem`` (its box unless lo / hi are given)."""
-        options.setdefault("lo", tuple(prob.lo))
-        options.setdefault("hi", tuple(prob.hi))
+        for key in ("lo", "hi"):
+            if getattr(prob, key, None) is not None:
+                options.setdefault(key, tuple(getattr(prob, key)))
         return cls(prob.x, prob.R, prob.omega, prob.w, prob.sigma_t, prob.sigma_s, prob.q,
                    inflow=prob.inflow, **options)
 
