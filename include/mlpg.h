@@ -97,6 +97,7 @@ typedef struct {
     double spmm_ms;              /* their device time (when timing is enabled), ms */
     int64_t spmm_bytes;          /* algorithmic bytes of one batched L-apply (active precision) */
     int64_t kernel_launches;     /* kernels this context launched since create */
+    int64_t device_bytes;        /* device memory this context holds (its own allocations) */
 } mlpg_stats;
 
 /* Default options (values listed in mlpg_options); a NULL opt is ignored.  A

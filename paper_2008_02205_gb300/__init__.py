@@ -56,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("last_refinements", ctypes.c_int32), ("last_residual", ctypes.c_double),
                 ("total_outer_iters", ctypes.c_int64), ("total_inner_iters", ctypes.c_int64),
                 ("spmm_launches", ctypes.c_int64), ("spmm_ms", ctypes.c_double),
-                ("spmm_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64)]
+                ("spmm_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -195,6 +195,7 @@ mlpg_status dalloc(mlpg_ctx *ctx, T **p, size_t count) {
         return set_err(ctx, MLPG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
     }
     ctx->allocs.push_back(q);
+    ctx->st.device_bytes += (int64_t)(count * sizeof(T));
     *p = static_cast<T *>(q);
     return MLPG_OK;
 }

@@ -35,6 +35,7 @@ class Request:
 class Result:
     request: Request
     flux: np.ndarray | None = None
+    device_bytes: int | None = None   # device memory the problem held at its last step (when known)
     admitted: float = 0.0
     finished: float = 0.0
     error: str | None = None
@@ -90,6 +91,9 @@ class LibraryBackend:
     def flux(self, h):
         return h.scalar_flux()
 
+    def device_bytes(self, h):
+        return int(h.stats()["device_bytes"])
+
     def close(self, h):
         h.close()
 
@@ -127,6 +131,9 @@ class Server:
                 res.flux = self.backend.flux(a[1])
             else:
                 res.error = error
+            measure = getattr(self.backend, "device_bytes", None)
+            if measure is not None:
+                res.device_bytes = measure(a[1])
             self.backend.close(a[1])
             res.finished = self.clock() - t0
             used -= a[2]

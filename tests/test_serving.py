@@ -192,3 +192,16 @@ def test_serves_a_poisson_stream_under_the_estimated_budget():
     assert srv.peak_active >= 2
     admitted = [r.admitted for r in sorted(res, key=lambda r: r.request.arrival)]
     assert admitted == sorted(admitted)
+
+
+def test_device_memory_is_recorded_when_the_backend_reports_it():
+    class Measured(FakeBackend):
+        def device_bytes(self, h):
+            return 1000 + self.steps[h]
+
+    clk, be = FakeClock(), Measured()
+    srv = Server(10, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size)
+    res = srv.run([Request(FakeProblem(2), steps=3, dt=0.1), Request(FakeProblem(1), steps=5, dt=0.1)])
+    assert [r.device_bytes for r in res] == [1003, 1005]     # taken after each problem's last step
+    res = _server(10)[0].run([Request(FakeProblem(1), steps=1, dt=0.1)])
+    assert res[0].device_bytes is None                       # a backend without the counter
