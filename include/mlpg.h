@@ -259,9 +259,12 @@ mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void
  * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.  The
  * scratch is one static device array of about 2.8 MB that every GPU loading
  * this library holds until the process exits; n > MLPG_NOALLOC_MAX_POINTS
- * returns MLPG_ERR_ARG.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the one array: calls
+ * returns MLPG_ERR_ARG, as do a non-finite or empty box.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture.  The kept address belongs to the device's
+ * primary context: after cudaDeviceReset on that device it is stale and the
+ * call must not be used again in that process.  All calls share the one array: calls
  * that overlap on the GPU (different streams, or host threads without
  * ordering) race and give wrong counts; order them on one stream.  Work is
  * queued on `stream` and the call returns without waiting. */

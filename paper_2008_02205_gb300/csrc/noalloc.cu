@@ -9,6 +9,7 @@
 // whose grid-binning scratch lives in one file-scope device array instead of
 // freshly allocated buffers.  The array is created when the library is loaded
 // and every GPU that loads the library keeps it until the process exits.
+#include <cmath>
 #include <mutex>
 
 #include "internal.h"
@@ -23,6 +24,9 @@ namespace {
 // ---- the static scratch and its layout (int32 words) -----------------------
 constexpr int64_t kMaxPts = MLPG_NOALLOC_MAX_POINTS;   // points per call
 constexpr int64_t kMaxCells = int64_t(1) << 16;        // grid bins per call
+constexpr int kSide2 = 256, kSide3 = 40;                // bins per axis at most: 256^2, 40^3 <= kMaxCells
+static_assert((int64_t)kSide2 * kSide2 <= kMaxCells && (int64_t)kSide3 * kSide3 * kSide3 <= kMaxCells,
+              "bin grid exceeds the scratch");
 constexpr int64_t kOffCellOf = 0;                       // [kMaxPts] bin of each point
 constexpr int64_t kOffPts = kOffCellOf + kMaxPts;       // [kMaxPts] points sorted by bin
 constexpr int64_t kOffCount = kOffPts + kMaxPts;        // [kMaxCells] points per bin
@@ -67,8 +71,12 @@ __device__ __forceinline__ int na_coord(double v, double lo, double inv, int gd)
     return c < 0 ? 0 : (c >= gd ? gd - 1 : c);
 }
 
-// Bin size 2 max(R) (every overlap partner lies in the 3^d bins around a
-// point), doubled until the bins fit the scratch.  One block.
+// Bin size g >= 2 max(R), so every overlap partner lies in the 3^d bins
+// around a point, and at least (largest box side) / kSide, so that at most
+// kSide bins lie along any axis and kSide^dim <= kMaxCells bins in all: no
+// iteration, and the bin count cannot exceed the scratch for any extents
+// (tiny, huge or not finite).  Points beyond the last bin are clamped into it,
+// which keeps every partner inside the 3^d stencil.  One block.
 __global__ void k_na_setup(int64_t n, int dim, const double *__restrict__ R, double3 lo, double3 hi,
                            int32_t *__restrict__ scratch) {
     __shared__ double sm[256];
@@ -83,18 +91,14 @@ __global__ void k_na_setup(int64_t n, int dim, const double *__restrict__ R, dou
     if (threadIdx.x != 0) return;
     GridParams *gp = reinterpret_cast<GridParams *>(scratch + kOffParams);
     const double l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
-    double g = 2.0 * sm[0];
-    if (!(g > 0.0)) g = h[0] - l[0];
+    const int side = dim == 2 ? kSide2 : kSide3;
+    double smax = 0.0;
+    for (int a = 0; a < dim; ++a) smax = fmax(smax, h[a] - l[a]);
+    double g = fmax(2.0 * sm[0], smax / side);   // fmax drops a NaN extent
     int gd[3] = {1, 1, 1};
-    for (int it = 0; it < 64; ++it) {
-        int64_t nc = 1;
-        for (int a = 0; a < dim; ++a) {
-            double cells = ceil((h[a] - l[a]) / g);
-            gd[a] = cells < 1.0 ? 1 : (cells > 1e9 ? 1000000000 : (int)cells);
-            nc *= gd[a];
-        }
-        if (nc <= kMaxCells) break;
-        g *= 2.0;
+    for (int a = 0; a < dim; ++a) {
+        const double cells = ceil((h[a] - l[a]) / g);   // <= side up to rounding
+        gd[a] = cells >= 1.0 ? (cells < (double)side ? (int)cells : side) : 1;
     }
     for (int a = 0; a < 3; ++a) gp->lo[a] = l[a];
     gp->inv = 1.0 / g;
@@ -188,7 +192,7 @@ extern "C" mlpg_status mlpg_overlap_counts_noalloc(int dim, int64_t n, const dou
     if ((dim != 2 && dim != 3) || n < 1 || !points || !kernel_extent || !lo || !hi || !counts) return MLPG_ERR_ARG;
     if (n > kMaxPts) return MLPG_ERR_ARG;   // beyond the static scratch
     for (int a = 0; a < dim; ++a)
-        if (!(hi[a] > lo[a])) return MLPG_ERR_ARG;
+        if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(hi[a] > lo[a])) return MLPG_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
