@@ -174,3 +174,73 @@ def test_lognormal_40_cubed_refined_full_size():
             Psi_prev = Psi
         phi = tp.scalar_flux(kind=1)
         assert np.all(np.isfinite(phi)) and phi.max() < 4 * math.pi * 1.1
+
+
+def _functions_per_tet(disc):
+    """Largest number of RK functions supported on one tetrahedron (the union
+    over its 8 quadrature points, which the oracle lists tetrahedron by
+    tetrahedron), from the oracle's own support lists."""
+    sptr, sidx, _, _ = O.rk_at_points(disc.x, disc.R, disc.V, disc.rowptr, disc.col, disc.vq.x, disc.vq.owner)
+    nq = len(disc.vq.w)
+    assert nq % 8 == 0
+    return max(len(np.unique(sidx[sptr[q]:sptr[q + 8]])) for q in range(0, nq, 8))
+
+
+@pytest.fixture(scope="module")
+def lattice12():
+    """12^3 jittered lattice (1,728 points, 64 of them at least four spacings
+    from every face), S4, lognormal sigma_t, inflow on x = 0."""
+    prob = _problem(12, seed=3012, steps=2, dt=0.02)
+    disc = O.Discretization(prob.x, prob.R, prob.lo, prob.hi)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    tr = O.Transport(disc, F, prob.omega, prob.w, psi_b=prob.inflow)
+    _, Phi_ref, _ = O.Solver(tr, outer_tol=1e-13).run(np.zeros((tr.M, disc.n)), prob.dt, prob.steps)
+    return prob, disc, F, Phi_ref
+
+
+def test_forms_3d_12_cubed_reach_the_interior_path(lattice12):
+    """Every integrated form element by element at 1e-12 of its array's
+    magnitude on a lattice whose interior tetrahedra carry the full 3D
+    support (the assembly's many-function path)."""
+    prob, disc, F, _ = lattice12
+    nfun = _functions_per_tet(disc)
+    print(f"12^3: largest number of functions on one tetrahedron: {nfun}")
+    assert nfun >= 40
+    with pkg.TransportProblem.from_problem(prob) as tp:
+        tp.integrate().assemble()
+        rowptr, col = tp.neighbors()
+        assert np.array_equal(rowptr, disc.rowptr) and np.array_equal(col, disc.col)
+        V = tp.volumes()
+        mats, vecs = tp.forms()
+    assert np.abs(V - disc.V).max() <= 1e-13 * disc.V.max()
+    d = 3
+    ref_m = np.concatenate([F["M0"][None], F["Mt"][None], F["Ms"][None], F["G"], F["Gt"], F["Gs"],
+                            F["K"].reshape(d * d, -1), F["S"]])
+    ref_v = np.concatenate([F["Q0"][None], F["Q"], F["B"]])
+    for k in range(ref_m.shape[0]):
+        assert np.abs(mats[k] - ref_m[k]).max() <= 1e-12 * np.abs(ref_m[k]).max(), k
+    for k in range(ref_v.shape[0]):
+        assert np.abs(vecs[k] - ref_v[k]).max() <= 1e-12 * max(np.abs(ref_v[k]).max(), 1e-300), k
+
+
+@pytest.mark.parametrize("precision,tol", [(pkg.MLPG_FP64, 1e-9), (pkg.MLPG_MIXED, 1e-8)])
+def test_run_3d_12_cubed_matches_oracle(lattice12, precision, tol):
+    prob, disc, F, Phi_ref = lattice12
+    ref = disc.interpolation_matrix() @ Phi_ref
+    with pkg.TransportProblem.from_problem(prob, precision=precision, inner_tol=1e-13, outer_tol=1e-13,
+                                           refine_tol=1e-12) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+        assert _rel(phi, ref) < tol
+        assert _rel(tp.scalar_flux(kind=1), Phi_ref) < tol
+
+
+def test_refined_run_3d_10_cubed_matches_oracle():
+    """Alg. 2 set (levels 0 -> 2 refined within 30 degrees of +x) on a 10^3
+    lattice in mixed precision against the oracle."""
+    prob = mi.lognormal_3d(10, seed=3010, steps=2, dt=0.02, refine=(0, 2, 30.0))
+    ref, _ = _oracle_run(prob)
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, refine_tol=1e-12) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+        assert _rel(phi, ref) < 1e-8
