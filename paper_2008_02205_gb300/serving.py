@@ -6,7 +6,9 @@ while the device memory they are estimated to need fits the budget and a
 slot is free, keeps every admitted problem's operators and flux state
 resident on the device, and advances all admitted problems together: each
 iteration is one ``mlpg_step_batch`` call, which steps every context on its
-own stream so that their kernels overlap.  A problem leaves as soon as its
+own stream so that their kernels overlap.  Admitted requests are set up
+(integration and assembly on their own streams) by a background thread, so
+that the resident problems keep stepping meanwhile.  A problem leaves as soon as its
 last step is done (its memory and slot go to the next arrivals), with its
 latency measured from its arrival.  A problem that cannot be set up, or whose
 step fails (an iteration cap, say), leaves with its error and its memory
@@ -71,6 +73,19 @@ class LibraryBackend:
     def __init__(self):
         import paper_2008_02205_gb300 as pkg
         self.pkg = pkg
+        # the device current in the scheduling thread: set-up threads create their contexts there
+        self.device = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                self.device = torch.cuda.current_device()
+        except ImportError:
+            pass
+
+    def thread_init(self):
+        if self.device is not None:
+            import torch
+            torch.cuda.set_device(self.device)
 
     def open(self, req: Request):
         tp = self.pkg.TransportProblem.from_problem(req.problem, **req.options)
@@ -107,22 +122,34 @@ class Server:
     close(handle)."""
 
     def __init__(self, hbm_budget_bytes: int, max_active: int = 16, backend=None, clock=time.perf_counter,
-                 estimate=estimate_bytes, sleep=time.sleep):
+                 estimate=estimate_bytes, sleep=time.sleep, open_workers: int = 1):
+        """open_workers > 0: admitted requests are set up (integrate +
+        assemble, on their own streams) by that many background threads while
+        the resident problems keep stepping; they join the batch once ready.
+        open_workers = 0: set up inline, in the scheduling thread."""
         self.budget = int(hbm_budget_bytes)
         self.max_active = int(max_active)
         self.backend = backend if backend is not None else LibraryBackend()
         self.clock = clock
         self.estimate = estimate
         self.sleep = sleep
+        self.open_workers = int(open_workers)
         self.peak_active = 0
         self.iterations = 0
+        self.steps_during_open = 0   # batched steps taken while some admitted request was being set up
 
     def run(self, requests):
         pending = sorted(requests, key=lambda r: r.arrival)
         results = {id(r): Result(r) for r in requests}
         active = []          # [request, handle, bytes, steps done]
+        opening = []         # [request, future, bytes]: admitted, being set up
         used = 0
         t0 = self.clock()
+        pool = None
+        if self.open_workers > 0:
+            from concurrent.futures import ThreadPoolExecutor
+            pool = ThreadPoolExecutor(max_workers=self.open_workers, thread_name_prefix="mlpg-open",
+                                      initializer=getattr(self.backend, "thread_init", None))
 
         def retire(a, error=None):
             nonlocal used
@@ -138,10 +165,20 @@ class Server:
             res.finished = self.clock() - t0
             used -= a[2]
 
+        def opened(req, need, handle=None, error=None):
+            nonlocal used
+            res = results[id(req)]
+            if error is not None:       # bad input, geometry, device memory: this request only
+                res.error = f"open failed: {error}"
+                res.finished = self.clock() - t0
+                used -= need
+            else:
+                active.append([req, handle, need, 0])
+
         try:
-            while pending or active:
+            while pending or active or opening:
                 now = self.clock() - t0
-                while pending and pending[0].arrival <= now and len(active) < self.max_active:
+                while pending and pending[0].arrival <= now and len(active) + len(opening) < self.max_active:
                     req = pending[0]
                     need = self.estimate(req.problem, req.options.get("precision", 0) == 1)   # 1: mixed
                     res = results[id(req)]
@@ -154,21 +191,39 @@ class Server:
                         break                   # wait for memory to free up (FIFO)
                     pending.pop(0)
                     res.admitted = self.clock() - t0
+                    used += need
+                    if pool is not None:
+                        opening.append([req, pool.submit(self.backend.open, req), need])
+                        continue
                     try:
                         handle = self.backend.open(req)
-                    except Exception as e:      # bad input, geometry, device memory: this request only
-                        res.error = f"open failed: {e}"
-                        res.finished = self.clock() - t0
+                    except Exception as e:
+                        opened(req, need, error=e)
                         continue
-                    active.append([req, handle, need, 0])
-                    used += need
+                    opened(req, need, handle)
+                # set-ups that finished join the batch
+                still = []
+                for o in opening:
+                    if o[1].done():
+                        try:
+                            opened(o[0], o[2], o[1].result())
+                        except Exception as e:
+                            opened(o[0], o[2], error=e)
+                    else:
+                        still.append(o)
+                opening = still
                 if not active:
-                    if pending:                 # idle until the next arrival
-                        wait = pending[0].arrival - (self.clock() - t0)
-                        if wait > 0:
-                            self.sleep(min(wait, 0.01))
+                    if opening:                 # nothing to step: wait for a set-up
+                        from concurrent.futures import FIRST_COMPLETED, wait
+                        wait([o[1] for o in opening], timeout=0.01, return_when=FIRST_COMPLETED)
+                    elif pending:               # idle until the next arrival
+                        wait_s = pending[0].arrival - (self.clock() - t0)
+                        if wait_s > 0:
+                            self.sleep(min(wait_s, 0.01))
                     continue
                 self.peak_active = max(self.peak_active, len(active))
+                if opening:
+                    self.steps_during_open += 1
                 errors = self.backend.step([a[1] for a in active], [a[0].dt for a in active])
                 if errors is None:
                     errors = [None] * len(active)
@@ -190,6 +245,13 @@ class Server:
                     self.backend.close(a[1])
                 except Exception:
                     pass
+            for o in opening:
+                try:
+                    self.backend.close(o[1].result())
+                except Exception:
+                    pass
+            if pool is not None:
+                pool.shutdown(wait=True)
         return [results[id(r)] for r in requests]
 
 

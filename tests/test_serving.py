@@ -51,7 +51,7 @@ class FakeBackend:
 def _server(budget, max_active=8):
     clk, be = FakeClock(), FakeBackend()
     srv = Server(budget, max_active=max_active, backend=be, clock=clk, sleep=clk.sleep,
-                 estimate=lambda p, mixed: p.size)
+                 estimate=lambda p, mixed: p.size, open_workers=0)
     return srv, be
 
 
@@ -132,7 +132,8 @@ class FailingBackend(FakeBackend):
 
 def _failing_server(budget, **kw):
     clk, be = FakeClock(), FailingBackend(**kw)
-    return Server(budget, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size), be
+    return Server(budget, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size,
+                  open_workers=0), be
 
 
 def test_a_request_that_cannot_be_opened_fails_alone():
@@ -162,7 +163,7 @@ def test_an_escaping_error_still_closes_every_context():
         def step(self, handles, dts):
             raise ValueError("bad batch")
     clk, be = FakeClock(), Boom()
-    srv = Server(10, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size)
+    srv = Server(10, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size, open_workers=0)
     import pytest
     with pytest.raises(ValueError):
         srv.run([Request(FakeProblem(1), steps=2, dt=0.1), Request(FakeProblem(2), steps=2, dt=0.1)])
@@ -200,8 +201,57 @@ def test_device_memory_is_recorded_when_the_backend_reports_it():
             return 1000 + self.steps[h]
 
     clk, be = FakeClock(), Measured()
-    srv = Server(10, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size)
+    srv = Server(10, backend=be, clock=clk, sleep=clk.sleep, estimate=lambda p, mixed: p.size, open_workers=0)
     res = srv.run([Request(FakeProblem(2), steps=3, dt=0.1), Request(FakeProblem(1), steps=5, dt=0.1)])
     assert [r.device_bytes for r in res] == [1003, 1005]     # taken after each problem's last step
     res = _server(10)[0].run([Request(FakeProblem(1), steps=1, dt=0.1)])
     assert res[0].device_bytes is None                       # a backend without the counter
+
+
+class SlowOpenBackend(FakeBackend):
+    """Set-up of the second request blocks until the first has taken three
+    steps: with background set-up the first keeps stepping meanwhile."""
+
+    def __init__(self):
+        super().__init__()
+        import threading
+        self.gate = threading.Event()
+
+    def open(self, req):
+        if req.problem.size == 2:
+            assert self.gate.wait(timeout=10.0)
+        return super().open(req)
+
+    def step(self, handles, dts):
+        import time
+        super().step(handles, dts)
+        if any(self.steps[h] >= 3 for h in handles):
+            self.gate.set()
+        time.sleep(0.002)                      # a step takes time: the set-up thread catches up
+
+
+def test_setup_runs_beside_the_resident_batch():
+    be = SlowOpenBackend()
+    reqs = [Request(FakeProblem(1), steps=200, dt=0.1, arrival=0.0),
+            Request(FakeProblem(2), steps=2, dt=0.1, arrival=0.0)]
+    srv = Server(10, backend=be, estimate=lambda p, mixed: p.size, open_workers=1)
+    res = srv.run(reqs)
+    assert all(r.error is None for r in res)
+    assert res[0].flux[0] == 200 and res[1].flux[0] == 2
+    assert srv.steps_during_open >= 3          # the first problem stepped while the second was set up
+    assert any(len(h) == 2 for h, _ in be.calls)
+
+
+def test_background_setup_failure_stays_with_its_request():
+    class Bad(FakeBackend):
+        def open(self, req):
+            if req.problem.size == 3:
+                raise RuntimeError("geometry")
+            return super().open(req)
+    be = Bad()
+    reqs = [Request(FakeProblem(1), steps=3, dt=0.1), Request(FakeProblem(3), steps=3, dt=0.1),
+            Request(FakeProblem(2), steps=3, dt=0.1)]
+    res = Server(10, backend=be, estimate=lambda p, mixed: p.size, open_workers=2).run(reqs)
+    assert res[1].error.startswith("open failed") and res[1].flux is None
+    assert res[0].flux[0] == 3 and res[2].flux[0] == 3
+    assert be.open_sizes == {}
