@@ -79,6 +79,25 @@ typedef struct {
                               neighbours, e.g. extent 2.5-3 point spacings); 3D: 1 only;
                               default 1 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
+    int apply_kernel;      /* MLPG_MIXED batched L-apply: 0 = automatic (row tiles when m % 4 == 0 and
+                              the tile's staged directions fit shared memory), 1 = one team of
+                              direction lanes per row gathering X through L1, 2 = row tiles with the
+                              tile's neighbour rows staged in shared memory (m % 4 == 0), 3 = the
+                              same tiles with the combination of the base arrays on tensor cores
+                              (TF32 split in high and low parts: FP32 accuracy; m % 8 == 0);
+                              default 0 */
+    int tile_rows;         /* row tiles: rows per tile, 32 or 64; 0 = 64 */
+    int tile_dpt;          /* row tiles: directions per thread, 4 or 8 (must divide m); 0 = 8 when
+                              m % 8 == 0, else 4 */
+    int outer_precond;     /* outer GMRES on Phi: 0 = none (the paper's), 1 = DSA-like diffusion
+                              correction, right preconditioner I + C^-1 Ms with the P1-diffusion
+                              operator C = diag(1/(3 sigma_t,i)) sum_a K_aa + kappa M0 + Mt - Ms
+                              + 1/2 sum_f S_f built from the integrated forms (Sec. 5.3 and Sec. 6
+                              name diffusion acceleration without deriving one); the outer GMRES is
+                              then flexible; needs outer_method 0; default 0 */
+    double dsa_tol;        /* outer_precond 1: tolerance of the FP64 diffusion solves; default 1e-10 */
+    int dsa_max;           /* outer_precond 1: iteration cap of a diffusion solve (its iterate is
+                              kept at the cap); default 500 */
 } mlpg_options;
 
 typedef struct {
@@ -98,6 +117,13 @@ typedef struct {
     int64_t spmm_bytes;          /* algorithmic bytes of one batched L-apply (active precision) */
     int64_t kernel_launches;     /* kernels this context launched since create */
     int64_t device_bytes;        /* device memory this context holds (its own allocations) */
+    int32_t apply_kernel;        /* FP32 batched L-apply in use once operators exist: 1 row teams,
+                                    2 row tiles, 3 row tiles on tensor cores (see
+                                    mlpg_options.apply_kernel); 0 before */
+    int32_t tile_chunk;          /* row tiles: directions per CTA (the chunk), 0 otherwise */
+    int64_t tile_max_halo;       /* row tiles: largest halo (staged neighbour rows) of a tile */
+    int64_t last_dsa_iters;      /* outer_precond 1: diffusion-solve iterations, last step */
+    int64_t total_dsa_iters;
 } mlpg_stats;
 
 /* Default options (values listed in mlpg_options); a NULL opt is ignored.  A
@@ -271,6 +297,24 @@ mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void
 mlpg_status mlpg_overlap_counts_noalloc(int dim, int64_t n, const double *points,
                                         const double *kernel_extent, const double *lo,
                                         const double *hi, int32_t *counts, void *stream);
+
+/* ---- direction shards ------------------------------------------------------ */
+
+/* Sum across direction shards (Sec. 4.2: L^-1 is block-diagonal in angle, so
+ * the directions of one problem can be split over several contexts, one per
+ * GPU, each created with its own subset of ordinates and weights).  The shards
+ * exchange only sums: the angular reduction D (an n-vector, once for the first
+ * flight and once per outer iteration, plus the state's scalar flux) and the
+ * two sums of squares of each FP64 step-residual norm.  The library calls
+ * fn(buf, count, user) with a HOST buffer of `count` doubles holding this
+ * shard's partial sums; fn must overwrite them with the sums over all shards
+ * and return 0.  Every shard calls fn equally often with equal counts, in the
+ * same order, because the outer solve is replicated on identical data.  A
+ * nonzero return fails the call in progress with MLPG_ERR_ARG ("cross-shard
+ * sum failed").  fn == NULL removes the callback (a single shard, the
+ * default).  Valid in any state; the caller keeps `user` alive. */
+typedef int (*mlpg_reduce_fn)(double *buf, int64_t count, void *user);
+mlpg_status mlpg_set_reduce(mlpg_ctx *ctx, mlpg_reduce_fn fn, void *user);
 
 /* Last error message of this context ("" when none; "null context" for NULL).
  * Valid until the next call on the context. */

@@ -45,7 +45,9 @@ class Options(ctypes.Structure):
                 ("mixed_inner_tol", ctypes.c_double), ("check_every", ctypes.c_int),
                 ("mixed_restart", ctypes.c_int), ("mixed_reorth", ctypes.c_int),
                 ("mixed_half_prec", ctypes.c_int), ("outer_method", ctypes.c_int), ("rk_order", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("apply_kernel", ctypes.c_int),
+                ("tile_rows", ctypes.c_int), ("tile_dpt", ctypes.c_int), ("outer_precond", ctypes.c_int),
+                ("dsa_tol", ctypes.c_double), ("dsa_max", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -57,7 +59,9 @@ class Stats(ctypes.Structure):
                 ("total_outer_iters", ctypes.c_int64), ("total_inner_iters", ctypes.c_int64),
                 ("spmm_launches", ctypes.c_int64), ("spmm_ms", ctypes.c_double),
                 ("spmm_bytes", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("apply_kernel", ctypes.c_int32), ("tile_chunk", ctypes.c_int32),
+                ("tile_max_halo", ctypes.c_int64), ("last_dsa_iters", ctypes.c_int64),
+                ("total_dsa_iters", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -100,6 +104,7 @@ def load_library(path: str = LIB_PATH):
         "mlpg_get_forms": (i32, [_P, _P, _P]),
         "mlpg_apply_L_dev": (i32, [_P, dbl, ctypes.c_int, _P, _P]),
         "mlpg_overlap_counts_noalloc": (i32, [ctypes.c_int, i64, _P, _P, _P, _P, _P, _P]),
+        "mlpg_set_reduce": (i32, [_P, _P, _P]),
         "mlpg_last_error": (ctypes.c_char_p, [_P]),
         "mlpg_destroy": (None, [_P]),
     }
@@ -298,6 +303,17 @@ def mlpg_overlap_counts_noalloc(dim, n, points_ptr, extent_ptr, lo, hi, counts_p
     hi_a = _arr(list(hi)[:dim])
     return load_library().mlpg_overlap_counts_noalloc(dim, n, points_ptr, extent_ptr, _ptr(lo_a), _ptr(hi_a),
                                                       counts_ptr, stream)
+
+
+# cross-shard sum callback: int fn(double *buf, int64_t count, void *user)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_void_p)
+
+
+def mlpg_set_reduce(ctx, fn):
+    """Install a cross-shard sum (a REDUCE_FN object, kept alive by the
+    caller) or remove it (None)."""
+    ptr = ctypes.cast(fn, _P) if fn is not None else None
+    _check(ctx, load_library().mlpg_set_reduce(ctx, ptr, None))
 
 
 def mlpg_last_error(ctx):

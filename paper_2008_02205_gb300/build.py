@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libmlpg.so")
 SOURCES = ["api.cu", "neighbors.cu", "assemble.cu", "assemble3d.cu", "cells2d.cu", "operators.cu", "krylov.cu", "noalloc.cu", "geometry.cpp",
-           "quadrature.cpp"]
+           "quadrature.cpp", "tiles.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,6 +23,30 @@ mlpg_status cuda_fail(mlpg_ctx *ctx, cudaError_t e, const char *what, const char
     return set_err(ctx, MLPG_ERR_CUDA, m);
 }
 
+mlpg_status shard_sum_host(mlpg_ctx *ctx, double *host, int64_t count) {
+    if (!ctx->reduce_fn) return MLPG_OK;
+    if (ctx->reduce_fn(host, count, ctx->reduce_user) != 0)
+        return set_err(ctx, MLPG_ERR_ARG, "cross-shard sum failed");
+    return MLPG_OK;
+}
+
+mlpg_status shard_sum_dev(mlpg_ctx *ctx, double *dev, int64_t count) {
+    if (!ctx->reduce_fn) return MLPG_OK;
+    if (count > ctx->n + 8) return set_err(ctx, MLPG_ERR_ARG, "cross-shard sum too long");
+    if (!ctx->reduce_host) {
+        void *hp = nullptr;
+        CU(ctx, cudaHostAlloc(&hp, sizeof(double) * (ctx->n + 8), cudaHostAllocDefault));
+        ctx->host_allocs.push_back(hp);
+        ctx->reduce_host = static_cast<double *>(hp);
+    }
+    CU(ctx, cudaMemcpyAsync(ctx->reduce_host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    MLPG_TRY(shard_sum_host(ctx, ctx->reduce_host, count));
+    CU(ctx, cudaMemcpyAsync(dev, ctx->reduce_host, sizeof(double) * count, cudaMemcpyHostToDevice, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));   // the host buffer is reused by the next sum
+    return MLPG_OK;
+}
+
 void harvest_timing(mlpg_ctx *ctx) {
     for (int k = 0; k < ctx->ev_used; ++k) {
         float ms = 0.f;
@@ -70,7 +94,12 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
         opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART ||
         (opt->mixed_reorth != 0 && opt->mixed_reorth != 1) ||
         (opt->mixed_half_prec != 0 && opt->mixed_half_prec != 1) || opt->rk_order < 0 || opt->rk_order > 2 ||
-        (opt->outer_method != 0 && opt->outer_method != 1) ||
+        (opt->outer_method != 0 && opt->outer_method != 1) || opt->apply_kernel < 0 || opt->apply_kernel > 3 ||
+        (opt->apply_kernel == 2 && (m & 3) != 0) || (opt->apply_kernel == 3 && (m & 7) != 0) ||
+        (opt->tile_rows != 0 && opt->tile_rows != 32 && opt->tile_rows != 64) ||
+        (opt->tile_dpt != 0 && opt->tile_dpt != 4 && opt->tile_dpt != 8) ||
+        (opt->outer_precond != 0 && opt->outer_precond != 1) || (opt->outer_precond == 1 && opt->outer_method != 0) ||
+        (opt->outer_precond == 1 && (!(opt->dsa_tol > 0.0) || opt->dsa_max < 1)) ||
         (opt->dim == 3 && opt->rk_order != 1) || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
@@ -218,6 +247,12 @@ void mlpg_default_options(mlpg_options *o) {
     o->outer_method = 0;
     o->rk_order = 1;
     o->stream = nullptr;
+    o->apply_kernel = 0;
+    o->tile_rows = 0;
+    o->tile_dpt = 0;
+    o->outer_precond = 0;
+    o->dsa_tol = 1e-10;
+    o->dsa_max = 500;
 }
 
 mlpg_status mlpg_create(const mlpg_options *opt, int64_t n, const double *points, const double *kernel_extent,
@@ -255,6 +290,7 @@ mlpg_status mlpg_set_initial(mlpg_ctx *ctx, const double *psi0) {
     else CU(ctx, cudaMemsetAsync(ctx->Psi, 0, N * sizeof(double), ctx->stream));
     k_phi_from_psi<<<(ctx->n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n, ctx->m, ctx->w, ctx->Psi, ctx->Phi);
     CU_LAUNCH(ctx);
+    MLPG_TRY(shard_sum_dev(ctx, ctx->Phi, ctx->n));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->nhist = 0;   // a new state: no history for the initial guess
     return MLPG_OK;
@@ -408,6 +444,9 @@ mlpg_status mlpg_get_stats(const mlpg_ctx *cctx, mlpg_stats *st) {
         ctx->st.spmm_bytes = nnz * (4 + na * 4) + ctx->nb * (4 + nf * 4) + 2 * 4 * (n + 1) + 2 * n * m * 4;
     else
         ctx->st.spmm_bytes = nnz * (4 + 8 * m) + 4 * (n + 1) + 2 * n * m * 8;
+    ctx->st.apply_kernel = ctx->A32 ? (ctx->t_rec ? (ctx->tile_mma ? 3 : 2) : 1) : 0;
+    ctx->st.tile_chunk = ctx->t_rec ? ctx->tile_chunk : 0;
+    ctx->st.tile_max_halo = ctx->t_rec ? ctx->tile_max_halo : 0;
     *st = ctx->st;
     return MLPG_OK;
 }
@@ -473,6 +512,13 @@ mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void
         return set_err(ctx, MLPG_ERR_ARG, "bad precision");
     }
     CATCH_ALL(ctx)
+}
+
+mlpg_status mlpg_set_reduce(mlpg_ctx *ctx, mlpg_reduce_fn fn, void *user) {
+    if (!ctx) return MLPG_ERR_ARG;
+    ctx->reduce_fn = fn;
+    ctx->reduce_user = fn ? user : nullptr;
+    return MLPG_OK;
 }
 
 const char *mlpg_last_error(const mlpg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }

@@ -50,6 +50,24 @@ struct HostCells3 {
 };
 int64_t build_cells_3d(int64_t n, const double *x, const double *R, const double *lo,
                        const double *hi, const int32_t *rowptr, const int32_t *col, HostCells3 &out);
+// Row tiles of the batched L-apply (tiles.cpp): Morton-consecutive rows, the
+// halo (union of their columns) and sliced-ELL record slots.
+struct TileLayout {
+    int rows_per_tile = 0;
+    int64_t ntile = 0;
+    std::vector<int64_t> base;    // ntile + 1: first record slot of each tile
+    std::vector<int32_t> width;   // ntile: entries per row slot (longest row of the tile, rounded up)
+    std::vector<int32_t> row;     // ntile * rows_per_tile: row of each row slot, -1 past n
+    std::vector<int64_t> hptr;    // ntile + 1: halo ranges in hcol
+    std::vector<int32_t> hcol;    // halo columns, sorted within each tile
+    std::vector<int32_t> perm;    // record slot -> pattern entry, -1 for padding
+    std::vector<int32_t> lcol;    // record slot -> halo index of its column (0 for padding)
+    int64_t max_halo = 0;
+    int32_t max_width = 0;
+};
+// order[n]: the rows in tile order.  Returns the number of record slots.
+int64_t build_tiles(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *order, int rows_per_tile,
+                    int width_multiple, TileLayout &out);
 // Reference rules (quadrature.cpp).
 void gauss_jacobi_newton(int n, double a, double b, double *t, double *w);
 void triangle_rule(int n1d, double *xi /*2*n1d^2*/, double *w);
@@ -81,6 +99,8 @@ struct Gmres {
     int *h_active = nullptr;   // pinned host mirror: number of active directions
     int *d_active_count = nullptr;
     bool reorth = true;        // CGS2 (true) or a single classical Gram-Schmidt pass
+    int its_slot = 0;          // iteration counter of the step this solve adds to (0 inner, 1 outer, 2 diffusion)
+    T *Zf = nullptr;           // R * n * M: preconditioned basis vectors (flexible GMRES), or null
 };
 
 }  // namespace mlpg
@@ -158,6 +178,12 @@ struct mlpg_ctx {
     mlpg::Gmres<double> g64;
     mlpg::Gmres<float> g32;
     mlpg::Gmres<double> gout;
+    mlpg::Gmres<double> gdsa;     // diffusion solves of the DSA-like outer preconditioner
+
+    // DSA-like outer preconditioner: diffusion operator on the pattern and its block inverses
+    double *Cdiff = nullptr;      // [nnz] FP64
+    double *Cinv = nullptr;       // [nblk][kBlockPts][kBlockPts] FP64
+    double *dsa_buf = nullptr;    // [2][n] work vectors
 
     double ops_psib[6] = {0, 0, 0, 0, 0, 0};  // inflow the operators were formed with
     int32_t *rowidx = nullptr;  // [nnz] row of each pattern entry
@@ -167,14 +193,32 @@ struct mlpg_ctx {
     int64_t nblk = 0;
     int32_t *bmember = nullptr; // [nblk * kBlockPts] point of each block slot (-1: empty)
     int32_t *bof = nullptr;     // [n] block * kBlockPts + slot of each point
+    std::vector<int32_t> h_order;  // [n] points in Morton order (host)
+
+    // row tiles of the FP32 L-apply (tiles.cpp), used when m % 4 == 0
+    int tile_rows = 0, tile_chunk = 0, tile_dpt = 0, tile_xs = 0;  // rows per tile, directions per CTA, per thread, smem row stride
+    bool tile_mma = false;      // the tensor-core variant of the tiled apply (apply_kernel 3)
+    int64_t ntile = 0, nslot = 0;
+    size_t tile_smem = 0;       // dynamic shared memory of the tiled kernel: halo rows + record stages
+    int tile_xs_f4 = 0;         // float4 words of the staged halo (the record stages follow)
+    int64_t tile_max_halo = 0;  // largest halo of a tile
+    int32_t *t_base = nullptr, *t_width = nullptr, *t_row = nullptr, *t_hptr = nullptr, *t_hcol = nullptr;
+    int32_t *t_perm = nullptr, *t_lcol = nullptr;
+    int32_t *t_bhalo = nullptr;  // [nb]: halo offset (index x tile_xs) of each boundary-segment entry's column
+    float *t_rec = nullptr;     // [nslot][rec words]: the base-array values of each slot, then its halo index
     float *Pinv = nullptr;      // [nblk][kBlockPts][kBlockPts][m] inverse diagonal blocks of L_m
     uint16_t *Pinv16 = nullptr; // same, FP16 bits scaled by Pscale^-1 (mixed mode), or null
     float *Pscale = nullptr;    // [nblk][m] power-of-two decode factor of each FP16 block
     double cur_inner_tol = 0.0; // tolerance of the inner solves inside the outer operator
-    long long *d_its = nullptr;  // [2] inner / outer Krylov iterations of the current step (device)
+    long long *d_its = nullptr;  // [3] inner / outer / diffusion Krylov iterations of the current step (device)
     void *bank64 = nullptr, *bank32 = nullptr;  // inner solutions of the outer basis (+ accumulator)
     double *hist[2] = {nullptr, nullptr};       // previous states for the initial guess
     int nhist = 0;                              // how many of them are valid
+
+    // direction shards: cross-shard sum callback and its pinned host buffer
+    mlpg_reduce_fn reduce_fn = nullptr;
+    void *reduce_user = nullptr;
+    double *reduce_host = nullptr;   // n + 8 doubles
 
     // stats
     mlpg_stats st{};
@@ -222,5 +266,16 @@ mlpg_status interp_flux(mlpg_ctx *ctx, double *out_dev, int kind);
 template <typename T>
 mlpg_status apply_prec(mlpg_ctx *ctx, T *v, T *z, const double *sc);
 mlpg_status build_blocks(mlpg_ctx *ctx);
+// Direction shards (api.cu): replace count partial sums by the sums over all
+// shards (a no-op without a callback).  shard_sum_dev works on a device vector
+// (synchronises the stream), shard_sum_host on host values.
+mlpg_status shard_sum_dev(mlpg_ctx *ctx, double *dev, int64_t count);
+mlpg_status shard_sum_host(mlpg_ctx *ctx, double *host, int64_t count);
+// DSA-like outer preconditioner (operators.cu): C for 1/(c dt) = kappa, y = C x or B - C x,
+// y = Ms x, and z = blockJacobi(C)^{-1} v (v first scaled in place by sc[0] when sc != null)
+mlpg_status form_diffusion(mlpg_ctx *ctx, double kappa);
+mlpg_status apply_C(mlpg_ctx *ctx, const double *X, const double *B, double *Y);
+mlpg_status apply_Ms_scalar(mlpg_ctx *ctx, const double *X, double *Y);
+mlpg_status apply_Cprec(mlpg_ctx *ctx, double *v, double *z, const double *sc);
 void harvest_timing(mlpg_ctx *ctx);
 }  // namespace mlpg

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <functional>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -41,10 +42,29 @@ Map2 map2(int M) {
     r.mchunks = (M + r.MB - 1) / r.MB;
     return r;
 }
-constexpr int kRowBlocks = 8 * 152;   // row blocks of the streaming passes (about 8 per SM)
+// multiprocessors of the current device (queried once per device)
+int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (!cache[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+            cudaGetLastError();
+            v = 152;
+        }
+        cache[dev] = v;
+    }
+    return cache[dev];
+}
+// row blocks of the streaming passes (about 8 per SM)
+int row_blocks() { return 8 * sm_count(); }
 int grid_rows(int64_t n, const Map2 &mp, int nl) {
     int64_t maxg = (n + mp.RB - 1) / mp.RB;
-    int64_t g = (kRowBlocks + mp.mchunks * nl - 1) / (mp.mchunks * nl);
+    int64_t g = (row_blocks() + mp.mchunks * nl - 1) / (mp.mchunks * nl);
     if (g > maxg) g = maxg;
     if (g < 1) g = 1;
     return (int)g;
@@ -241,6 +261,134 @@ static void launch_cgs(dim3 grid, cudaStream_t s, int64_t n, int M, int MB, int 
     else if (nl <= 8) k_cgs<T, 8, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
     else if (nl <= 16) k_cgs<T, 16, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
     else k_cgs<T, 32, MODE><<<grid, kBlock, 0, s>>>(n, M, MB, RB, nl, V, vs, hin, w, partial);
+}
+
+// Vectorised Gram-Schmidt passes (M a multiple of VEC = 16 / sizeof(T)):
+// thread (r, q) owns directions q*VEC .. q*VEC + VEC - 1 of the rows
+// r, r + RB, ... of its block's row stride and moves them with 16-byte loads.
+//   k_cgsv_dots:  h_l = V_l . w for l in group blockIdx.y (kDotGroup vectors
+//                 per group, so that the accumulators stay in registers; w is
+//                 re-read by each group, mostly from L2)
+//   k_cgsv_upd:   w <- w - sum_{l < nl} hin_l V_l, then ||w||^2 (hin staged
+//                 in shared memory)
+// Block sums go to partial[(l * M + m) * G + block], G = gridDim.x.
+constexpr int kDotGroup = 8;
+constexpr int kDsaRestart = 30;   // restart length of the diffusion solves
+constexpr size_t kUpdSmem = 96 * 1024;   // largest staged Hessenberg column block of k_cgsv_upd
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+__device__ __forceinline__ void unpack(const float4 &v, float *o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+__device__ __forceinline__ void unpack(const double2 &v, double *o) { o[0] = v.x; o[1] = v.y; }
+__device__ __forceinline__ float4 pack4(const float *o) { return make_float4(o[0], o[1], o[2], o[3]); }
+__device__ __forceinline__ double2 pack2(const double *o) { return make_double2(o[0], o[1]); }
+template <typename T> __device__ __forceinline__ typename Vec16<T>::type pack(const T *o);
+template <> __device__ __forceinline__ float4 pack<float>(const float *o) { return pack4(o); }
+template <> __device__ __forceinline__ double2 pack<double>(const double *o) { return pack2(o); }
+
+// Block sums of `nacc` accumulators per thread (VEC components each) over the
+// RB row slots, staged through shared memory kDotGroup accumulators at a time.
+template <typename T, int VEC>
+__device__ __forceinline__ void block_sums(const T (*acc)[VEC], int nacc, int l0, int M, int MQ, int RB, bool act,
+                                           double *__restrict__ partial, int G) {
+    __shared__ T sh[kDotGroup * kBlock * VEC];
+    const int t = threadIdx.x, q = t % MQ, r = t / MQ;
+    const int RM = RB * M;   // staged values per accumulator
+    for (int a0 = 0; a0 < nacc; a0 += kDotGroup) {
+        const int na = min(kDotGroup, nacc - a0);
+        if (act)
+            for (int a = 0; a < na; ++a)
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) sh[a * RM + r * M + q * VEC + c] = acc[a0 + a][c];
+        __syncthreads();
+        for (int o = t; o < na * M; o += kBlock) {
+            const int a = o / M, m = o - a * M;
+            double sum = 0.0;
+            for (int k = 0; k < RB; ++k) sum += (double)sh[a * RM + k * M + m];
+            partial[((int64_t)(l0 + a0 + a) * M + m) * G + blockIdx.x] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgsv_dots(int64_t n, int M, int nl, const T *__restrict__ V, int64_t vs,
+                                                      const T *__restrict__ w, double *__restrict__ partial) {
+    using A = typename Arith<T>::type;
+    using V16 = typename Vec16<T>::type;
+    constexpr int VEC = Vec16<T>::n;
+    const int MQ = M / VEC, RB = kBlock / MQ, G = gridDim.x;
+    const int t = threadIdx.x, q = t % MQ, r = t / MQ;
+    const bool act = r < RB;
+    const int l0 = blockIdx.y * kDotGroup, nlg = min(kDotGroup, nl - l0);
+    A acc[kDotGroup][VEC];
+#pragma unroll
+    for (int a = 0; a < kDotGroup; ++a)
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) acc[a][c] = 0;
+    if (act) {
+        const int64_t stride = (int64_t)G * RB;
+        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += stride) {
+            const int64_t e = i * M + q * VEC;
+            T wv[VEC];
+            unpack(__ldg(reinterpret_cast<const V16 *>(w + e)), wv);
+#pragma unroll
+            for (int a = 0; a < kDotGroup; ++a) {
+                if (a < nlg) {
+                    T v[VEC];
+                    unpack(__ldg(reinterpret_cast<const V16 *>(V + (l0 + a) * vs + e)), v);
+#pragma unroll
+                    for (int c = 0; c < VEC; ++c) acc[a][c] += (A)v[c] * (A)wv[c];
+                }
+            }
+        }
+    }
+    block_sums<A, VEC>(acc, nlg, l0, M, MQ, RB, act, partial, G);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cgsv_upd(int64_t n, int M, int nl, const T *__restrict__ V, int64_t vs,
+                                                     const double *__restrict__ hin, T *__restrict__ w,
+                                                     double *__restrict__ partial) {
+    using A = typename Arith<T>::type;
+    using V16 = typename Vec16<T>::type;
+    constexpr int VEC = Vec16<T>::n;
+    extern __shared__ unsigned char smem_h[];
+    A *hs = reinterpret_cast<A *>(smem_h);   // [nl][M]
+    const int MQ = M / VEC, RB = kBlock / MQ, G = gridDim.x;
+    const int t = threadIdx.x, q = t % MQ, r = t / MQ;
+    const bool act = r < RB;
+    for (int k = t; k < nl * M; k += kBlock) hs[k] = (A)hin[k];
+    __syncthreads();
+    A acc[1][VEC];
+#pragma unroll
+    for (int c = 0; c < VEC; ++c) acc[0][c] = 0;
+    if (act) {
+        const int64_t stride = (int64_t)G * RB;
+        for (int64_t i = blockIdx.x * (int64_t)RB + r; i < n; i += stride) {
+            const int64_t e = i * M + q * VEC;
+            T wt[VEC];
+            unpack(*reinterpret_cast<const V16 *>(w + e), wt);
+            A wv[VEC];
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) wv[c] = (A)wt[c];
+#pragma unroll 4
+            for (int l = 0; l < nl; ++l) {
+                T v[VEC];
+                unpack(__ldg(reinterpret_cast<const V16 *>(V + l * vs + e)), v);
+                const A *hl = hs + l * M + q * VEC;
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) wv[c] -= hl[c] * (A)v[c];
+            }
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) {
+                wt[c] = (T)wv[c];
+                acc[0][c] += (A)wt[c] * (A)wt[c];
+            }
+            *reinterpret_cast<V16 *>(w + e) = pack<T>(wt);
+        }
+    }
+    block_sums<A, VEC>(acc, 1, 0, M, MQ, RB, act, partial, G);
 }
 
 // Start of a cycle: beta = ||r|| (nrm2 = ||r||^2); decide which systems iterate.
@@ -477,8 +625,12 @@ inline int64_t nblk(int64_t N) { return (N + kBlock - 1) / kBlock; }
 // workspace
 // ---------------------------------------------------------------------------
 template <typename T>
-static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int R) {
-    if (G.n == n && G.M == M && G.R == R) return MLPG_OK;
+static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int R, bool flexible = false) {
+    if (G.n == n && G.M == M && G.R == R && (!flexible || G.Zf)) return MLPG_OK;
+    if (G.n == n && G.M == M && G.R == R) {   // the same shape: only the flexible buffer is new
+        MLPG_TRY(dalloc(ctx, &G.Zf, (size_t)R * n * M));
+        return MLPG_OK;
+    }
     if (R > MLPG_MAX_RESTART || R < 1) return set_err(ctx, MLPG_ERR_ARG, "restart length out of range");
     G.n = n; G.M = M; G.R = R;
     MLPG_TRY(dalloc(ctx, &G.V, (size_t)(R + 1) * n * M));
@@ -499,10 +651,12 @@ static mlpg_status gmres_alloc(mlpg_ctx *ctx, Gmres<T> &G, int64_t n, int M, int
     MLPG_TRY(dalloc(ctx, &G.active, M));
     MLPG_TRY(dalloc(ctx, &G.kcol, M));
     MLPG_TRY(dalloc(ctx, &G.its, M));
-    // the fused Gram-Schmidt passes write G * nl * M partials with G <= kRowBlocks, nl <= R + 1
-    G.partial_cap = (int64_t)kRowBlocks * (R + 1) * M;
+    // the fused Gram-Schmidt passes write G * nl * M partials with G <= row_blocks(), nl <= R + 1
+    G.partial_cap = (int64_t)row_blocks() * (R + 1) * M;
     MLPG_TRY(dalloc(ctx, &G.partial, G.partial_cap));
     MLPG_TRY(dalloc(ctx, &G.d_active_count, 1));
+    if (flexible) MLPG_TRY(dalloc(ctx, &G.Zf, (size_t)R * n * M));
+    CU(ctx, cudaFuncSetAttribute(k_cgsv_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem));
     void *hp = nullptr;
     CU(ctx, cudaHostAlloc(&hp, sizeof(int) * 4, cudaHostAllocDefault));
     ctx->host_allocs.push_back(hp);
@@ -532,6 +686,10 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
     cudaStream_t s = ctx->stream;
     const Map2 mp = map2(M);
     const int wblk = (int)((M * 32 + kBlock - 1) / kBlock);
+    using Ar = typename Arith<T>::type;
+    constexpr int VEC = Vec16<T>::n;
+    const bool vec_ok = M % VEC == 0 && M / VEC <= kBlock;
+    const int64_t vrows = vec_ok ? (n + kBlock / (M / VEC) - 1) / (kBlock / (M / VEC)) : 1;   // row iterations
     CU(ctx, cudaMemsetAsync(G.its, 0, sizeof(int) * M, s));
     auto norm2 = [&](const T *v) -> mlpg_status {   // G.nrm2[m] = ||v_m||^2
         int g1 = grid_rows(n, mp, 1);
@@ -580,10 +738,11 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
             if (*G.h_active == 0) break;
         }
         if ((int64_t)cycle * R >= max_its) {
-            k_add_its<<<1, 32, 0, s>>>(M, G.its, ctx->d_its);
+            k_add_its<<<1, 32, 0, s>>>(M, G.its, ctx->d_its + G.its_slot);
             return set_err(ctx, MLPG_ERR_NOT_CONVERGED, "GMRES reached its iteration cap");
         }
-        const T *z = precond(G.V, G.Z, G.beta);
+        // flexible GMRES keeps every preconditioned basis vector (the preconditioner may change between applies)
+        const T *z = precond(G.V, G.Zf ? G.Zf : G.Z, G.beta);
         if (!z) return MLPG_ERR_CUDA;
         int jlast = 0;
         for (int j = 0; j < R; ++j) {
@@ -591,10 +750,28 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
             if (slot) *slot = j;                      // operator applied to basis vector j
             MLPG_TRY(A(z, nullptr, w));
             int gnorm = 0;
-            {
+            const int nl = j + 1;
+            if (vec_ok && !G.reorth && (size_t)nl * M * sizeof(Ar) <= kUpdSmem) {
+                // single classical pass, 16-byte vectors: dots (groups of kDotGroup
+                // basis vectors per grid row), reduce, update + norm partials
+                const int ng = (nl + kDotGroup - 1) / kDotGroup;
+                // two blocks per SM: enough loads in flight, few partial sums for k_reduce / k_givens
+                const int gd = (int)std::max<int64_t>(1, std::min<int64_t>(vrows, (2 * sm_count() + ng - 1) / ng));
+                if ((int64_t)gd * nl * M > G.partial_cap || (int64_t)2 * sm_count() * M > G.partial_cap)
+                    return set_err(ctx, MLPG_ERR_ARG, "reduction buffer too small");
+                k_cgsv_dots<T><<<dim3(gd, ng), kBlock, 0, s>>>(n, M, nl, G.V, vs, w, G.partial);
+                CU_LAUNCH(ctx);
+                k_reduce<<<(int)(((int64_t)nl * M * 32 + kBlock - 1) / kBlock), kBlock, 0, s>>>(M, nl, gd, G.partial,
+                                                                                              G.h);
+                CU_LAUNCH(ctx);
+                const int gu = (int)std::max<int64_t>(1, std::min<int64_t>(vrows, 2 * sm_count()));
+                k_cgsv_upd<T><<<gu, kBlock, (size_t)nl * M * sizeof(Ar), s>>>(n, M, nl, G.V, vs, G.h, w, G.partial);
+                CU_LAUNCH(ctx);
+                gnorm = gu;
+            } else {
                 // CGS2 in three fused passes over V_0..V_j (CGS1: two passes, h2 unused)
                 // fewer, longer-running blocks as the basis grows (bounded partial sums)
-                const int nl = j + 1, g1 = grid_rows(n, mp, (nl + 3) / 4);
+                const int g1 = grid_rows(n, mp, (nl + 3) / 4);
                 const dim3 grid(g1, mp.mchunks);
                 if ((int64_t)g1 * nl * mp.mchunks * mp.MB > G.partial_cap)
                     return set_err(ctx, MLPG_ERR_ARG, "reduction buffer too small");
@@ -624,21 +801,28 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
                 CU(ctx, cudaStreamSynchronize(s));
                 if (*G.h_active == 0) break;
             }
-            z = precond(w, G.Z, G.beta);
+            if (j + 1 == R) break;   // no next basis vector in this cycle
+            z = precond(w, G.Zf ? G.Zf + (int64_t)(j + 1) * N : G.Z, G.beta);
             if (!z) return MLPG_ERR_CUDA;
         }
         k_backsolve<<<(M + 127) / 128, 128, 0, s>>>(M, R, G.H, G.g, G.kcol, G.y, G.y32);
         CU_LAUNCH(ctx);
         if (on_cycle) MLPG_TRY(on_cycle(G.y, G.y32, G.kcol, jlast + 1));
-        k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, y_of<T>(G), G.kcol, G.W);
-        CU_LAUNCH(ctx);
-        const T *u = precond(G.W, G.Z, nullptr);
-        if (!u) return MLPG_ERR_CUDA;
+        const T *u = G.W;
+        if (G.Zf) {   // x += sum_l y_l z_l
+            k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.Zf, vs, y_of<T>(G), G.kcol, G.W);
+            CU_LAUNCH(ctx);
+        } else {      // x += P^{-1} sum_l y_l v_l
+            k_combine<T><<<nblk(N), kBlock, 0, s>>>(n, M, jlast + 1, G.V, vs, y_of<T>(G), G.kcol, G.W);
+            CU_LAUNCH(ctx);
+            u = precond(G.W, G.Z, nullptr);
+            if (!u) return MLPG_ERR_CUDA;
+        }
         k_axpy1<T><<<nblk(N), kBlock, 0, s>>>(N, u, x);
         CU_LAUNCH(ctx);
     }
     // iteration counts stay on the device (summed into ctx->d_its, read once per step)
-    k_add_its<<<1, 32, 0, s>>>(M, G.its, ctx->d_its + (M == 1 ? 1 : 0));
+    k_add_its<<<1, 32, 0, s>>>(M, G.its, ctx->d_its + G.its_slot);
     CU_LAUNCH(ctx);
     *iters = total;
     return MLPG_OK;
@@ -716,6 +900,33 @@ static mlpg_status outer_bank(mlpg_ctx *ctx, int R, T **bank, T **xacc) {
     return MLPG_OK;
 }
 
+// DSA-like right preconditioner of the outer solve: z = v + C^{-1} Ms v, the
+// scattering source of the Krylov direction v driving a diffusion correction
+// (C: form_diffusion).  The diffusion system is solved by FP64 GMRES with
+// block-Jacobi (the blocks of C), to dsa_tol; the outer GMRES is flexible, so
+// an inexact diffusion solve changes iterations, not the solution.
+static mlpg_status dsa_precond(mlpg_ctx *ctx, double *v, double *z, const double *sc) {
+    const int64_t n = ctx->n;
+    cudaStream_t s = ctx->stream;
+    if (sc) {
+        k_scale<double><<<nblk(n), kBlock, 0, s>>>(n, 1, v, sc);
+        CU_LAUNCH(ctx);
+    }
+    double *rhs = ctx->dsa_buf, *y = ctx->dsa_buf + n;
+    MLPG_TRY(apply_Ms_scalar(ctx, v, rhs));
+    MLPG_TRY(gmres_alloc(ctx, ctx->gdsa, n, 1, kDsaRestart));
+    ctx->gdsa.its_slot = 2;
+    CU(ctx, cudaMemsetAsync(y, 0, sizeof(double) * n, s));
+    ApplyFn<double> A = [ctx](const double *X, const double *B, double *Y) { return apply_C(ctx, X, B, Y); };
+    PrecFn<double> P = [ctx](double *vv, double *zz, const double *ss) { return apply_Cprec(ctx, vv, zz, ss); };
+    int64_t its = 0;
+    MLPG_TRY(gmres_solve<double>(ctx, ctx->gdsa, A, P, rhs, y, ctx->opt.dsa_tol, ctx->opt.dsa_max, 5, &its,
+                                 CycleFn(), nullptr, true, true));
+    k_add<double, double><<<nblk(n), kBlock, 0, s>>>(n, v, y, z);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
 // Nested solve of (L - MS D) Psi = f (Sec. 4.2): first flight, GMRES on Phi,
 // recovery.  f and Psi are FP64 [n][m]; inner solves run in T.  Phi_io holds
 // the initial guess of Phi on entry (may be null) and the result on exit.
@@ -743,8 +954,11 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     MLPG_TRY(inner_solve<T>(ctx, rhs, bpsi, inner_tol));
     k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, bpsi, bphi);
     CU_LAUNCH(ctx);
+    MLPG_TRY(shard_sum_dev(ctx, bphi, n));
     // scattering GMRES: (I - D L^{-1} MS) Phi = b_phi
-    MLPG_TRY(gmres_alloc(ctx, ctx->gout, n, 1, ctx->opt.outer_restart));
+    const bool dsa = ctx->opt.outer_precond == 1;
+    MLPG_TRY(gmres_alloc(ctx, ctx->gout, n, 1, ctx->opt.outer_restart, dsa));
+    ctx->gout.its_slot = 1;
     if (Phi_io) CU(ctx, cudaMemcpyAsync(phi, Phi_io, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     else CU(ctx, cudaMemsetAsync(phi, 0, sizeof(double) * n, s));
     if (ctx->opt.outer_method == 1) {
@@ -760,6 +974,7 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
             MLPG_TRY(inner_solve<T>(ctx, rhs, x, inner_tol));
             k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, x, d);
             CU_LAUNCH(ctx);
+            MLPG_TRY(shard_sum_dev(ctx, d, n));
             k_si_update<<<nblk(n), kBlock, 0, s>>>(n, bphi, d, phi, e);
             CU_LAUNCH(ctx);
             k_bump<<<1, 1, 0, s>>>(ctx->d_its + 1);
@@ -793,6 +1008,7 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
         MLPG_TRY(inner_solve<T>(ctx, rhs, xt, ctx->cur_inner_tol));
         k_Dreduce<T><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, xt, d);
         CU_LAUNCH(ctx);
+        MLPG_TRY(shard_sum_dev(ctx, d, n));
         k_outer_combine<<<nblk(n), kBlock, 0, s>>>(n, X, d, B, Y);
         CU_LAUNCH(ctx);
         return MLPG_OK;
@@ -814,7 +1030,9 @@ static mlpg_status nested_solve(mlpg_ctx *ctx, const double *f, double *Psi_out,
     // decides convergence, and the inexact inner solves inside the operator
     // can hold the outer residual near its own tolerance.
     const bool correction = sizeof(T) == 4;
-    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, PrecFn<double>(), bphi, phi, outer_tol,
+    PrecFn<double> Pout;
+    if (dsa) Pout = [ctx](double *v, double *z, const double *sc) { return dsa_precond(ctx, v, z, sc); };
+    MLPG_TRY(gmres_solve<double>(ctx, ctx->gout, A, Pout, bphi, phi, outer_tol,
                                  correction ? Rout : ctx->opt.max_outer, 1, &oits, on_cycle, &slot, phi_zero,
                                  correction));
     (void)oits;
@@ -850,8 +1068,9 @@ static mlpg_status reset_step_stats(mlpg_ctx *ctx) {
     ctx->st.last_inner_iters = 0;
     ctx->st.last_inner_solves = 0;
     ctx->st.last_refinements = 0;
-    if (!ctx->d_its) MLPG_TRY(dalloc(ctx, &ctx->d_its, 2));
-    CU(ctx, cudaMemsetAsync(ctx->d_its, 0, 2 * sizeof(long long), ctx->stream));
+    ctx->st.last_dsa_iters = 0;
+    if (!ctx->d_its) MLPG_TRY(dalloc(ctx, &ctx->d_its, 3));
+    CU(ctx, cudaMemsetAsync(ctx->d_its, 0, 3 * sizeof(long long), ctx->stream));
     return MLPG_OK;
 }
 
@@ -866,16 +1085,18 @@ static mlpg_status prepare_step(mlpg_ctx *ctx, double dt) {
 }
 
 static void finish_step_stats(mlpg_ctx *ctx) {
-    long long its[2] = {0, 0};
+    long long its[3] = {0, 0, 0};
     if (cudaMemcpyAsync(its, ctx->d_its, sizeof(its), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
         cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
         ctx->st.last_inner_iters = its[0];
         ctx->st.last_outer_iters = (int32_t)its[1];
+        ctx->st.last_dsa_iters = its[2];
     }
     cudaGetLastError();
     ctx->st.steps += 1;
     ctx->st.total_outer_iters += ctx->st.last_outer_iters;
     ctx->st.total_inner_iters += ctx->st.last_inner_iters;
+    ctx->st.total_dsa_iters += ctx->st.last_dsa_iters;
 }
 
 mlpg_status step_fp64(mlpg_ctx *ctx, double dt) {
@@ -887,6 +1108,7 @@ mlpg_status step_fp64(mlpg_ctx *ctx, double dt) {
     CU(ctx, cudaMemcpyAsync(ctx->Psi, ctx->tmp64, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     k_Dreduce<double><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, ctx->Psi, ctx->Phi);
     CU_LAUNCH(ctx);
+    MLPG_TRY(shard_sum_dev(ctx, ctx->Phi, n));
     // report the FP64 step residual
     MLPG_TRY(apply_L64_res(ctx, ctx->Psi, ctx->f64, ctx->res64));
     MLPG_TRY(apply_MS<double>(ctx, ctx->Phi, ctx->tmp64));
@@ -895,6 +1117,7 @@ mlpg_status step_fp64(mlpg_ctx *ctx, double dt) {
     MLPG_TRY(global_norm(ctx, ctx->res64, N, ctx->h_red));
     MLPG_TRY(global_norm(ctx, ctx->f64, N, ctx->h_red + 1));
     CU(ctx, cudaStreamSynchronize(s));
+    MLPG_TRY(shard_sum_host(ctx, ctx->h_red, 2));
     ctx->st.last_residual = ctx->h_red[1] > 0 ? std::sqrt(ctx->h_red[0] / ctx->h_red[1]) : 0.0;
     finish_step_stats(ctx);
     return MLPG_OK;
@@ -931,12 +1154,15 @@ mlpg_status step_mixed(mlpg_ctx *ctx, double dt) {
     for (;; ++k) {
         k_Dreduce<double><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, ctx->Psi, phi_c);
         CU_LAUNCH(ctx);
+        MLPG_TRY(shard_sum_dev(ctx, phi_c, n));
         MLPG_TRY(apply_L64_res(ctx, ctx->Psi, ctx->f64, ctx->res64));
         MLPG_TRY(apply_MS<double>(ctx, phi_c, ctx->tmp64));
         k_add<double, double><<<nblk(N), kBlock, 0, s>>>(N, ctx->res64, ctx->tmp64, ctx->res64);
         CU_LAUNCH(ctx);
         MLPG_TRY(global_norm(ctx, ctx->res64, N, ctx->h_red));
         CU(ctx, cudaStreamSynchronize(s));
+        if (k == 0) MLPG_TRY(shard_sum_host(ctx, ctx->h_red + 1, 1));   // ||f||^2, once per step
+        MLPG_TRY(shard_sum_host(ctx, ctx->h_red, 1));
         rel = ctx->h_red[1] > 0 ? std::sqrt(ctx->h_red[0] / ctx->h_red[1]) : 0.0;
         if (rel <= ctx->opt.refine_tol) break;
         if (k >= ctx->opt.max_refine) {
@@ -950,6 +1176,7 @@ mlpg_status step_mixed(mlpg_ctx *ctx, double dt) {
     }
     k_Dreduce<double><<<nblk(n * 32), kBlock, 0, s>>>(n, ctx->m, ctx->w, ctx->Psi, ctx->Phi);
     CU_LAUNCH(ctx);
+    MLPG_TRY(shard_sum_dev(ctx, ctx->Phi, n));
     ctx->st.last_refinements = k;
     ctx->st.last_residual = rel;
     finish_step_stats(ctx);

@@ -441,6 +441,219 @@ __global__ void __launch_bounds__(256) k_faces32(int64_t nbr, int m, int tm_log2
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled FP32 L-apply (m % 4 == 0).  One CTA per (row tile, direction chunk):
+//   1. the tile's halo rows of X (the union of its rows' columns, mc of the m
+//      directions) are copied into shared memory once with 16-byte cp.async;
+//   2. thread (s, g) owns row slot s of the tile and DPT directions of the
+//      chunk (quads g and g + G, G = mc / DPT, so that the threads of one row
+//      read one contiguous run of the staged row); it walks the tile's
+//      sliced-ELL records (the K base-array values of an entry and its halo
+//      index; the rows of a warp read adjacent records), combines the K values
+//      with its directions' coefficients and accumulates value x X from shared
+//      memory, two directions per packed FP32 FMA;
+//   3. Y = L X, or Y = B - L X, is written for its row and directions.
+// The outflow-face terms of the boundary rows are added by k_faces32.
+// ---------------------------------------------------------------------------
+template <int D>
+__host__ __device__ constexpr int rec_words() { return (NA<D>() + 4) / 4 * 4; }   // K values + halo index, padded to float4
+
+template <int D>
+__global__ void k_tile_records(int64_t nslot, int64_t nnz, int xs, const int32_t *__restrict__ perm,
+                               const int32_t *__restrict__ lcol, const float *__restrict__ A32,
+                               float4 *__restrict__ rec) {
+    constexpr int K = NA<D>(), RW = rec_words<D>();
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nslot) return;
+    const int32_t p = perm[e];
+    float v[RW];
+#pragma unroll
+    for (int k = 0; k < RW; ++k) v[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = p >= 0 ? A32[k * nnz + p] : 0.0f;
+    v[K] = __int_as_float(lcol[e] * xs);   // offset of the column's staged row in shared memory (floats)
+#pragma unroll
+    for (int q = 0; q < RW / 4; ++q) rec[e * (RW / 4) + q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+constexpr int kRecK = 4;        // record pipeline: entries (k steps) per stage
+constexpr int kRecStages = 4;   // record pipeline: stages in flight
+// direction groups per row: threads per CTA = rows per tile x groups (<= 640)
+__host__ __device__ constexpr int tile_max_groups(int tr, int dpt) { return (dpt == 8 ? 320 : 640) / tr; }
+// shared memory of one stage of records (TR rows per tile), in float4
+template <int D, int TR>
+__host__ __device__ constexpr int rec_stage_f4() { return kRecK * TR * (rec_words<D>() / 4); }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Records of stage st (entries st*kRecK .. +kRecK of every row slot) from the
+// tile's contiguous sliced-ELL block into buffer `buf`, reordered to
+// [float4 q][entry k][row slot s] so that the rows of a warp read
+// consecutive 16-byte words (no bank conflicts).
+template <int D, int TR>
+__device__ __forceinline__ void stage_records(float4 *Rs, int buf, const float4 *__restrict__ rg, int st, int W) {
+    constexpr int RW4 = rec_words<D>() / 4;
+    const int k0 = st * kRecK;
+    if (k0 >= W) return;
+    constexpr int cnt = kRecK * TR * RW4;   // W is a multiple of kRecK
+    const float4 *src = rg + (int64_t)k0 * TR * RW4;
+    float4 *dst = Rs + buf * rec_stage_f4<D, TR>();
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+        const int q = idx % RW4, ks = idx / RW4;   // ks = k * TR + s
+        cp_async16(dst + q * (kRecK * TR) + ks, src + idx);
+    }
+}
+
+template <int D, int DPT, int TR>
+__global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
+    int m, int mc, int xs, int xs_f4, const int32_t *__restrict__ base, const int32_t *__restrict__ width,
+    const int32_t *__restrict__ trow, const int32_t *__restrict__ hptr, const int32_t *__restrict__ hcol,
+    const float4 *__restrict__ rec, const float *__restrict__ coef32, const int32_t *__restrict__ bptr,
+    const int32_t *__restrict__ bhalo, const float *__restrict__ bval, int64_t nb, const float *__restrict__ X,
+    const float *__restrict__ B, float *__restrict__ Y) {
+    constexpr int K = NA<D>(), RW4 = rec_words<D>() / 4, NQ = DPT / 4;
+    extern __shared__ float4 smem_x4[];
+    float *Xs = reinterpret_cast<float *>(smem_x4);
+    float4 *Rs = smem_x4 + xs_f4;
+    const int t = blockIdx.x;
+    const int m0 = blockIdx.y * mc;
+    const int mcw = min(mc, m - m0);   // directions of this chunk (a multiple of 4)
+    const int G = mc / DPT;
+    const int s = threadIdx.x / G, g = threadIdx.x - s * G;
+    // 1. stage the halo rows (chunk columns m0 .. m0 + mcw): the first copy
+    //    group.  Thread (s, g) copies quads g, g + G, ... of halo rows s, s + TR, ...
+    {
+        const int h0 = hptr[t], hn = hptr[t + 1] - h0, q4 = mcw >> 2;
+        for (int hh = s; hh < hn; hh += TR) {
+            const float *src = X + (int64_t)hcol[h0 + hh] * m + m0;
+            for (int qq = g; qq < q4; qq += G) cp_async16(Xs + hh * xs + 4 * qq, src + 4 * qq);
+        }
+        cp_async_commit();
+    }
+    // 2. record pipeline prologue: stages 0 .. kRecStages - 2, one copy group each
+    const int W = width[t], nst = W / kRecK;
+    const float4 *rg = rec + (int64_t)base[t] * RW4;
+#pragma unroll
+    for (int st = 0; st < kRecStages - 1; ++st) {
+        stage_records<D, TR>(Rs, st, rg, st, W);
+        cp_async_commit();
+    }
+    // the thread's directions: quad g and (DPT = 8) quad g + G of the chunk
+    int qoff[NQ];
+    bool on[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+        qoff[u] = 4 * (g + u * G);
+        on[u] = qoff[u] < mcw;
+    }
+    float2 c[K][2 * NQ];   // coefficient pairs of the K - 1 direction-dependent arrays (c[0] unused)
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d0 = m0 + (on[u] ? qoff[u] : 0) + 2 * h;
+#pragma unroll
+            for (int k = 1; k < K; ++k) c[k][2 * u + h] = make_float2(coef32[16 * d0 + k], coef32[16 * (d0 + 1) + k]);
+        }
+    float2 acc[2 * NQ];
+#pragma unroll
+    for (int j = 0; j < 2 * NQ; ++j) acc[j] = make_float2(0.0f, 0.0f);
+    // 3. the entries, kRecK per stage (tile widths are multiples of kRecK:
+    //    padding slots hold zeros); stage st + kRecStages - 1 is copied while
+    //    st is used
+    for (int st = 0; st < nst; ++st) {
+        cp_async_wait<kRecStages - 2>();   // the halo and stage st have landed
+        __syncthreads();                   // ... for every thread; buffer (st - 1) % kRecStages is free
+        stage_records<D, TR>(Rs, (st + kRecStages - 1) % kRecStages, rg, st + kRecStages - 1, W);
+        cp_async_commit();
+        const float4 *rb = Rs + (st % kRecStages) * rec_stage_f4<D, TR>() + s;
+#pragma unroll
+        for (int kk = 0; kk < kRecK; ++kk) {
+            float a[4 * RW4];
+#pragma unroll
+            for (int q = 0; q < RW4; ++q) {
+                const float4 v = rb[q * (kRecK * TR) + kk * TR];
+                a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
+            }
+            const float *xr = Xs + __float_as_int(a[K]);
+            float2 ab[K];                  // the entry's values, each in both halves of a pair
+#pragma unroll
+            for (int k2 = 0; k2 < K; ++k2) ab[k2] = make_float2(a[k2], a[k2]);
+#pragma unroll
+            for (int u = 0; u < NQ; ++u) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(xr + qoff[u]);
+                const float2 xp[2] = {make_float2(x4.x, x4.y), make_float2(x4.z, x4.w)};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float2 v = ab[0];
+#pragma unroll
+                    for (int k2 = 1; k2 < K; ++k2) v = __ffma2_rn(c[k2][2 * u + h], ab[k2], v);
+                    acc[2 * u + h] = __ffma2_rn(v, xp[h], acc[2 * u + h]);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();   // no copy outlives the CTA
+    const int32_t row = trow[(int64_t)t * TR + s];
+    if (row < 0) return;
+    // 4. outflow-face terms of a boundary row: sum_f max(Omega . n_f, 0) (S_f X)_i
+    //    over the row's boundary-segment entries, whose columns are in the halo
+    const int32_t q0 = bptr[row], q1 = bptr[row + 1];
+    if (q1 > q0) {
+        float2 fc[NF<D>()][2 * NQ];
+#pragma unroll
+        for (int u = 0; u < NQ; ++u)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int d0 = m0 + (on[u] ? qoff[u] : 0) + 2 * h;
+#pragma unroll
+                for (int f = 0; f < NF<D>(); ++f)
+                    fc[f][2 * u + h] = make_float2(coef32[16 * d0 + face_slot<D>() + f],
+                                                   coef32[16 * (d0 + 1) + face_slot<D>() + f]);
+            }
+        for (int32_t q = q0; q < q1; ++q) {
+            const float *xr = Xs + bhalo[q];
+            float2 sv[NF<D>()];
+#pragma unroll
+            for (int f = 0; f < NF<D>(); ++f) {
+                const float v = bval[f * nb + q];
+                sv[f] = make_float2(v, v);
+            }
+#pragma unroll
+            for (int u = 0; u < NQ; ++u) {
+                const float4 x4 = *reinterpret_cast<const float4 *>(xr + qoff[u]);
+                const float2 xp[2] = {make_float2(x4.x, x4.y), make_float2(x4.z, x4.w)};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float2 v = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int f = 0; f < NF<D>(); ++f) v = __ffma2_rn(fc[f][2 * u + h], sv[f], v);
+                    acc[2 * u + h] = __ffma2_rn(v, xp[h], acc[2 * u + h]);
+                }
+            }
+        }
+    }
+    // 5. write the row
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+        if (!on[u]) continue;
+        const int64_t e = (int64_t)row * m + m0 + qoff[u];
+        float4 o = make_float4(acc[2 * u].x, acc[2 * u].y, acc[2 * u + 1].x, acc[2 * u + 1].y);
+        if (B) {
+            const float4 b = *reinterpret_cast<const float4 *>(B + e);
+            o = make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
+        }
+        *reinterpret_cast<float4 *>(Y + e) = o;
+    }
+}
+
 __global__ void k_brows(int64_t n, const int32_t *__restrict__ bptr, int32_t *__restrict__ brow,
                         int *__restrict__ count) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -807,6 +1020,338 @@ __global__ void __launch_bounds__(256) k_bjacobi_scalar(int64_t nblk, int m, con
     }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled FP32 L-apply on tensor cores (m % 8 == 0).  The same tiles, halo
+// staging and record pipeline as k_spmm32_tile; one warp per 16 row slots of
+// the tile.  For each entry step k, the combination of the K base arrays with
+// the direction coefficients,
+//     V[s][d] = sum_k a_k(s, k) c_k(d)      (16 rows x 8 directions per n-tile),
+// is a small matrix product: one mma.m16n8k8 per n-tile (two for K = 10),
+// operands split into high and low TF32 parts, hi*hi + hi*lo + lo*hi
+// accumulated in FP32, which keeps FP32 accuracy.  The B columns of n-tile
+// pair (2i, 2i+1) are mapped to directions so that the D values a lane holds
+// for the pair are four consecutive directions 16i + 4t .. 16i + 4t + 3: one
+// 16-byte shared load of the staged X row per pair and row, then
+// Y[s][d] += V[s][d] X[col][d] in packed FP32 FMAs (no reduction across lanes:
+// lane (g, t) owns rows g and g + 8 of its warp's slots).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+}
+// x = hi + lo with both parts representable in TF32
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+    hi = tf32_bits(x);
+    lo = tf32_bits(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// chunk direction of column n of n-tile j: pairs (2i, 2i+1) interleaved by
+// lane quads, a last odd n-tile in order
+__host__ __device__ __forceinline__ int mma_dir(int j, int n, int nt) {
+    const int np = nt / 2;
+    if (j >= 2 * np) return 16 * np + n;
+    return 16 * (j >> 1) + 4 * (n >> 1) + 2 * (j & 1) + (n & 1);
+}
+
+template <int D, int TR, int NT>
+__global__ void __launch_bounds__(2 * TR) k_spmm32_mma(
+    int m, int xs, int xs_f4, const int32_t *__restrict__ base, const int32_t *__restrict__ width,
+    const int32_t *__restrict__ trow, const int32_t *__restrict__ hptr, const int32_t *__restrict__ hcol,
+    const float4 *__restrict__ rec, const float *__restrict__ coef32, const int32_t *__restrict__ bptr,
+    const int32_t *__restrict__ bhalo, const float *__restrict__ bval, int64_t nb, const float *__restrict__ X,
+    const float *__restrict__ B, float *__restrict__ Y) {
+    constexpr int K = NA<D>(), KS = (K + 7) / 8, RW4 = rec_words<D>() / 4, MC = 8 * NT, NP = NT / 2;
+    extern __shared__ float4 smem_x4[];
+    float *Xs = reinterpret_cast<float *>(smem_x4);
+    float4 *Rs = smem_x4 + xs_f4;
+    const int t = blockIdx.x, m0 = blockIdx.y * MC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+    // 1. stage the halo rows of the chunk (first copy group)
+    {
+        const int h0 = hptr[t], hn = hptr[t + 1] - h0;
+        constexpr int Q4 = MC / 4;
+        for (int idx = threadIdx.x; idx < hn * Q4; idx += 2 * TR) {
+            const int hh = idx / Q4, qq = idx - hh * Q4;
+            cp_async16(Xs + hh * xs + 4 * qq, X + (int64_t)hcol[h0 + hh] * m + m0 + 4 * qq);
+        }
+        cp_async_commit();
+    }
+    // 2. record pipeline prologue
+    const int W = width[t], nst = W / kRecK;
+    const float4 *rg = rec + (int64_t)base[t] * RW4;
+#pragma unroll
+    for (int st = 0; st < kRecStages - 1; ++st) {
+        stage_records<D, TR>(Rs, st, rg, st, W);
+        cp_async_commit();
+    }
+    // B fragments (coefficients, split into TF32 hi and lo): B[k][n] = c_k(dir(j, n)), c_0 = 1
+    uint32_t bh[NT][KS][2], bl[NT][KS][2];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        const int d = m0 + mma_dir(j, g, NT);
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = ks * 8 + q + 4 * h;
+                const float c = k == 0 ? 1.0f : (k < K ? coef32[16 * d + k] : 0.0f);
+                tf32_split(c, bh[j][ks][h], bl[j][ks][h]);
+            }
+    }
+    float acc[2][NT][2];   // rows g, g + 8; per n-tile the lane's two directions
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[r][j][0] = acc[r][j][1] = 0.0f;
+    const int s0 = warp * 16 + g;   // this lane's row slots s0, s0 + 8
+    // 3. entry steps
+    for (int st = 0; st < nst; ++st) {
+        cp_async_wait<kRecStages - 2>();
+        __syncthreads();
+        stage_records<D, TR>(Rs, (st + kRecStages - 1) % kRecStages, rg, st + kRecStages - 1, W);
+        cp_async_commit();
+        const float *rb = reinterpret_cast<const float *>(Rs + (st % kRecStages) * rec_stage_f4<D, TR>());
+#pragma unroll
+        for (int kk = 0; kk < kRecK; ++kk) {
+            // word w of (entry kk, slot s) sits at float (w / 4) * 4 kRecK TR + 4 (kk TR + s) + w % 4
+            auto word = [&](int w, int sl) {
+                return rb[(w >> 2) * 4 * kRecK * TR + 4 * (kk * TR + sl) + (w & 3)];
+            };
+            const int lc0 = __float_as_int(word(K, s0)), lc1 = __float_as_int(word(K, s0 + 8));
+            float dv[NT][4];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) dv[j][0] = dv[j][1] = dv[j][2] = dv[j][3] = 0.0f;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const int w0 = ks * 8 + q, w1 = w0 + 4;
+                const float a0 = w0 < K ? word(w0, s0) : 0.0f, a1 = w0 < K ? word(w0, s0 + 8) : 0.0f;
+                const float a2 = w1 < K ? word(w1, s0) : 0.0f, a3 = w1 < K ? word(w1, s0 + 8) : 0.0f;
+                uint32_t ah[4], al[4];
+                tf32_split(a0, ah[0], al[0]);
+                tf32_split(a1, ah[1], al[1]);
+                tf32_split(a2, ah[2], al[2]);
+                tf32_split(a3, ah[3], al[3]);
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    mma_tf32(dv[j], al, bh[j][ks][0], bh[j][ks][1]);
+                    mma_tf32(dv[j], ah, bl[j][ks][0], bl[j][ks][1]);
+                    mma_tf32(dv[j], ah, bh[j][ks][0], bh[j][ks][1]);
+                }
+            }
+            // dv[j] = {V[g][2q], V[g][2q+1], V[g+8][2q], V[g+8][2q+1]} of n-tile j
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                const float4 x0 = *reinterpret_cast<const float4 *>(Xs + lc0 + 16 * i + 4 * q);
+                const float4 x1 = *reinterpret_cast<const float4 *>(Xs + lc1 + 16 * i + 4 * q);
+                acc[0][2 * i][0] = fmaf(dv[2 * i][0], x0.x, acc[0][2 * i][0]);
+                acc[0][2 * i][1] = fmaf(dv[2 * i][1], x0.y, acc[0][2 * i][1]);
+                acc[0][2 * i + 1][0] = fmaf(dv[2 * i + 1][0], x0.z, acc[0][2 * i + 1][0]);
+                acc[0][2 * i + 1][1] = fmaf(dv[2 * i + 1][1], x0.w, acc[0][2 * i + 1][1]);
+                acc[1][2 * i][0] = fmaf(dv[2 * i][2], x1.x, acc[1][2 * i][0]);
+                acc[1][2 * i][1] = fmaf(dv[2 * i][3], x1.y, acc[1][2 * i][1]);
+                acc[1][2 * i + 1][0] = fmaf(dv[2 * i + 1][2], x1.z, acc[1][2 * i + 1][0]);
+                acc[1][2 * i + 1][1] = fmaf(dv[2 * i + 1][3], x1.w, acc[1][2 * i + 1][1]);
+            }
+            if constexpr (NT & 1) {
+                constexpr int j = NT - 1;
+                const float2 x0 = *reinterpret_cast<const float2 *>(Xs + lc0 + 16 * NP + 2 * q);
+                const float2 x1 = *reinterpret_cast<const float2 *>(Xs + lc1 + 16 * NP + 2 * q);
+                acc[0][j][0] = fmaf(dv[j][0], x0.x, acc[0][j][0]);
+                acc[0][j][1] = fmaf(dv[j][1], x0.y, acc[0][j][1]);
+                acc[1][j][0] = fmaf(dv[j][2], x1.x, acc[1][j][0]);
+                acc[1][j][1] = fmaf(dv[j][3], x1.y, acc[1][j][1]);
+            }
+        }
+    }
+    cp_async_wait<0>();
+    // 4. face terms and the write, for the lane's two rows
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int32_t row = trow[(int64_t)t * TR + s0 + 8 * r];
+        if (row < 0) continue;
+        for (int32_t bq = bptr[row]; bq < bptr[row + 1]; ++bq) {
+            const float *xr = Xs + bhalo[bq];
+            float sv[NF<D>()];
+#pragma unroll
+            for (int f = 0; f < NF<D>(); ++f) sv[f] = bval[f * nb + bq];
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int d = mma_dir(j, 2 * q + e, NT);
+                    const float *fc = coef32 + 16 * (m0 + d) + face_slot<D>();
+                    float v = 0.0f;
+#pragma unroll
+                    for (int f = 0; f < NF<D>(); ++f) v = fmaf(fc[f], sv[f], v);
+                    acc[r][j][e] = fmaf(v, xr[d], acc[r][j][e]);
+                }
+        }
+        const int64_t rb0 = (int64_t)row * m + m0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const int64_t e = rb0 + 16 * i + 4 * q;
+            float4 o = make_float4(acc[r][2 * i][0], acc[r][2 * i][1], acc[r][2 * i + 1][0], acc[r][2 * i + 1][1]);
+            if (B) {
+                const float4 b = *reinterpret_cast<const float4 *>(B + e);
+                o = make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
+            }
+            *reinterpret_cast<float4 *>(Y + e) = o;
+        }
+        if constexpr (NT & 1) {
+            constexpr int j = NT - 1;
+            const int64_t e = rb0 + 16 * NP + 2 * q;
+            float2 o = make_float2(acc[r][j][0], acc[r][j][1]);
+            if (B) {
+                const float2 b = *reinterpret_cast<const float2 *>(B + e);
+                o = make_float2(b.x - o.x, b.y - o.y);
+            }
+            *reinterpret_cast<float2 *>(Y + e) = o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diffusion operator of the DSA-like outer preconditioner (FP64, on the
+// overlap pattern), built from the forms already integrated:
+//   C = diag(1 / (3 sigma_t,i)) sum_a K_aa + kappa M0 + (Mt - Ms) + 1/2 sum_f S_f,
+// sigma_t,i = (Mt 1)_i / (M0 1)_i, the test-function average of sigma_t: a
+// Galerkin P1-diffusion operator with the Marshak vacuum condition on every
+// face.  The paper names diffusion acceleration as the remedy for slow outer
+// solves (Sec. 5.3, Sec. 6) without deriving one.
+// ---------------------------------------------------------------------------
+template <int D>
+__global__ void k_diff_values(int64_t n, int64_t nnz, double kappa, const int32_t *__restrict__ rowptr,
+                              const double *__restrict__ mats, double *__restrict__ C) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double *M0 = mats, *Mt = mats + nnz, *Ms = mats + 2 * nnz;
+    const double *K = mats + (3 + 3 * D) * nnz, *S = mats + mat_S<D>() * nnz;
+    double st = 0.0, m0 = 0.0;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        st += Mt[p];
+        m0 += M0[p];
+    }
+    const double dco = m0 / (3.0 * st);   // 1 / (3 sigma_t,i)
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+        double kk = 0.0, sf = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) kk += K[(a * D + a) * nnz + p];
+#pragma unroll
+        for (int f = 0; f < NF<D>(); ++f) sf += S[f * nnz + p];
+        C[p] = dco * kk + kappa * M0[p] + (Mt[p] - Ms[p]) + 0.5 * sf;
+    }
+}
+
+// Inverse of the diagonal block (MLPG_BLOCK_PTS Morton points) of one FP64
+// operator on the pattern: one warp per block, Gauss-Jordan with partial
+// pivoting on [A | I] in shared memory, lane l owning column l.
+__global__ void __launch_bounds__(256) k_block_inv64(int64_t nblk, const int32_t *__restrict__ rowptr,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ A,
+                                                     const int32_t *__restrict__ bmember,
+                                                     const int32_t *__restrict__ bof, double *__restrict__ Pinv,
+                                                     int *__restrict__ flag) {
+    __shared__ double sA[8][kB][2 * kB + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t k = blockIdx.x * 8 + warp;
+    if (k >= nblk) return;
+    double(*W)[2 * kB + 1] = sA[warp];
+    if (lane < kB) {
+        const int a = lane;
+        for (int b = 0; b < 2 * kB; ++b) W[a][b] = (b == kB + a) ? 1.0 : 0.0;
+        const int32_t i = bmember[k * kB + a];
+        if (i < 0) {
+            W[a][a] = 1.0;
+        } else {
+            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                const int32_t sl = bof[col[p]];
+                if (sl / kB == k) W[a][sl - k * kB] = A[p];
+            }
+        }
+    }
+    __syncwarp();
+    for (int cc = 0; cc < kB; ++cc) {
+        int piv = cc;
+        double best = fabs(W[cc][cc]);
+        for (int r = cc + 1; r < kB; ++r) {
+            const double v = fabs(W[r][cc]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (!(best > 0.0)) {
+            if (lane == 0) atomicOr(flag, 64);
+            return;
+        }
+        __syncwarp();
+        if (piv != cc) {
+            const double t = W[cc][lane];
+            W[cc][lane] = W[piv][lane];
+            W[piv][lane] = t;
+        }
+        __syncwarp();
+        const double inv = 1.0 / W[cc][cc];
+        __syncwarp();
+        W[cc][lane] *= inv;
+        __syncwarp();
+        double fr[kB];
+#pragma unroll
+        for (int r = 0; r < kB; ++r) fr[r] = W[r][cc];
+        __syncwarp();
+        const double pc = W[cc][lane];
+#pragma unroll
+        for (int r = 0; r < kB; ++r)
+            if (r != cc) W[r][lane] -= fr[r] * pc;
+        __syncwarp();
+    }
+    for (int e = lane; e < kB * kB; e += 32) {
+        const int a = e / kB, b = e - a * kB;
+        Pinv[(k * kB + a) * kB + b] = W[a][kB + b];
+    }
+}
+
+// z = P^{-1} v for one vector (block-Jacobi with FP64 block inverses); with
+// sc != null, v is first scaled in place by sc[0].  One CTA of kB threads per
+// block.
+__global__ void __launch_bounds__(kB) k_bjacobi64_vec(int64_t nblk, const int32_t *__restrict__ bmember,
+                                                      const double *__restrict__ Pinv, double *__restrict__ v,
+                                                      const double *__restrict__ sc, double *__restrict__ z) {
+    __shared__ double vs[kB];
+    const int64_t blk = blockIdx.x;
+    const int a = threadIdx.x;
+    const int32_t i = bmember[blk * kB + a];
+    double val = 0.0;
+    if (i >= 0) {
+        val = v[i];
+        if (sc) {
+            val *= sc[0];
+            v[i] = val;
+        }
+    }
+    vs[a] = val;
+    __syncthreads();
+    if (i < 0) return;
+    const double *P = Pinv + (blk * kB + a) * kB;
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b < kB; ++b) acc = fma(P[b], vs[b], acc);
+    z[i] = acc;
+}
+
+// y = A x (B == null) or y = B - A x: FP64 CSR times one vector
+__global__ void k_csr_spmv64(int64_t n, const int32_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                             const double *__restrict__ A, const double *__restrict__ x,
+                             const double *__restrict__ B, double *__restrict__ y) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s = fma(A[p], x[col[p]], s);
+    y[i] = B ? B[i] - s : s;
+}
+
 struct Team {
     int tm_log2, dpl;
 };
@@ -841,6 +1386,179 @@ Team pick_team(int m) {
 // one warp per row (slot layout) / one team of TM lanes per row
 static int64_t team_grid(int64_t n, const Team &) { return (n * 32 + 255) / 256; }
 static int64_t rowteam_grid(int64_t n, const Team &tm) { return ((n << tm.tm_log2) + 255) / 256; }
+
+// Row tiles of the FP32 L-apply: built once per point set when m % 4 == 0.
+// Tile shape: TR rows per tile (32 or 64) and DPT directions per thread (8
+// when m % 8 == 0, else 4), from the options or, by default, 64 rows and the
+// larger DPT; G = chunk / DPT thread groups per row.  The directions are split
+// into chunks (one CTA each) until a tile's staged halo, halo x (chunk + 4)
+// floats, and the record stages fit kTileSmem.
+constexpr size_t kTileSmem = 100 * 1024;
+
+template <int D, int DPT, int TR>
+static mlpg_status launch_tile(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
+    const dim3 tg((unsigned)ctx->ntile, (unsigned)((ctx->m + ctx->tile_chunk - 1) / ctx->tile_chunk));
+    const int threads = TR * (ctx->tile_chunk / DPT);
+    k_spmm32_tile<D, DPT, TR><<<tg, threads, ctx->tile_smem, ctx->stream>>>(
+        ctx->m, ctx->tile_chunk, ctx->tile_xs, ctx->tile_xs_f4, ctx->t_base, ctx->t_width, ctx->t_row, ctx->t_hptr,
+        ctx->t_hcol, reinterpret_cast<const float4 *>(ctx->t_rec), ctx->coef32, ctx->bptr, ctx->t_bhalo, ctx->bval32,
+        ctx->nb, X, B, Y);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+template <int D, int TR, int NT>
+static mlpg_status launch_mma(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
+    const dim3 tg((unsigned)ctx->ntile, (unsigned)(ctx->m / (8 * NT)));
+    k_spmm32_mma<D, TR, NT><<<tg, 2 * TR, ctx->tile_smem, ctx->stream>>>(
+        ctx->m, ctx->tile_xs, ctx->tile_xs_f4, ctx->t_base, ctx->t_width, ctx->t_row, ctx->t_hptr, ctx->t_hcol,
+        reinterpret_cast<const float4 *>(ctx->t_rec), ctx->coef32, ctx->bptr, ctx->t_bhalo, ctx->bval32, ctx->nb, X,
+        B, Y);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+#define MMA_NT_SWITCH(D, TR, FN, ...)                   \
+    switch (ctx->tile_chunk / 8) {                      \
+        case 2: return FN<D, TR, 2>(__VA_ARGS__);       \
+        case 3: return FN<D, TR, 3>(__VA_ARGS__);       \
+        case 4: return FN<D, TR, 4>(__VA_ARGS__);       \
+        case 5: return FN<D, TR, 5>(__VA_ARGS__);       \
+        default: return FN<D, TR, 6>(__VA_ARGS__);      \
+    }
+template <int D, int TR, int NT>
+static mlpg_status mma_attr(mlpg_ctx *ctx) {
+    CU(ctx, cudaFuncSetAttribute(k_spmm32_mma<D, TR, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kTileSmem));
+    return MLPG_OK;
+}
+
+template <int D>
+static mlpg_status run_tile(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
+    if (ctx->tile_mma) {
+        if (ctx->tile_rows == 32) { MMA_NT_SWITCH(D, 32, launch_mma, ctx, X, B, Y) }
+        MMA_NT_SWITCH(D, 64, launch_mma, ctx, X, B, Y)
+    }
+    const int key = ctx->tile_dpt * 100 + ctx->tile_rows;
+    switch (key) {
+        case 832: return launch_tile<D, 8, 32>(ctx, X, B, Y);
+        case 864: return launch_tile<D, 8, 64>(ctx, X, B, Y);
+        case 432: return launch_tile<D, 4, 32>(ctx, X, B, Y);
+        default: return launch_tile<D, 4, 64>(ctx, X, B, Y);
+    }
+}
+template <int D, int DPT, int TR>
+static mlpg_status tile_attr(mlpg_ctx *ctx) {
+    // the kernel's attribute is shared by every context: set to the fixed budget, never lowered
+    CU(ctx, cudaFuncSetAttribute(k_spmm32_tile<D, DPT, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kTileSmem));
+    return MLPG_OK;
+}
+
+template <int D>
+static mlpg_status init_tiles(mlpg_ctx *ctx) {
+    const int m = ctx->m;
+    if ((m & 3) != 0 || ctx->opt.apply_kernel == 1) return MLPG_OK;
+    const int tr = ctx->opt.tile_rows ? ctx->opt.tile_rows : 64;
+    const int dpt = ctx->opt.tile_dpt ? ctx->opt.tile_dpt : ((m & 7) == 0 ? 8 : 4);
+    if (m % dpt != 0) return set_err(ctx, MLPG_ERR_ARG, "tile_dpt must divide the number of directions");
+    TileLayout tl;
+    const int64_t nslot = build_tiles(ctx->n, ctx->h_rowptr.data(), ctx->h_col.data(), ctx->h_order.data(), tr,
+                                      kRecK, tl);
+    if (nslot * (int64_t)(rec_words<D>() / 4) >= (int64_t(1) << 31) || tl.hptr.back() >= (int64_t(1) << 31))
+        return MLPG_OK;   // beyond 32-bit slot indices: the row-team kernel serves
+    const size_t rec_smem = (size_t)kRecStages * kRecK * tr * (rec_words<D>() / 4) * sizeof(float4);
+    int chunk = 0;
+    const bool mma = ctx->opt.apply_kernel == 3;
+    if (mma) {
+        // tensor-core tiles: chunks of 8 NT directions (NT <= 6) dividing m; shared-memory row stride
+        // 16 mod 32 words (two rows read by one 8-lane phase then fall on disjoint banks half the time)
+        if ((m & 7) != 0) return set_err(ctx, MLPG_ERR_ARG, "apply_kernel 3 needs a multiple of 8 directions");
+        for (int nt = 6; nt >= 2 && !chunk; --nt) {
+            const int mc = 8 * nt, xs = mc + (16 - mc % 32 + 32) % 32;
+            if (m % mc == 0 && (size_t)tl.max_halo * xs * sizeof(float) + rec_smem <= kTileSmem) chunk = mc;
+        }
+        if (!chunk) return set_err(ctx, MLPG_ERR_ARG, "apply_kernel 3: no direction chunk fits shared memory");
+    }
+    for (int nchunk = 1; nchunk <= m / 4 && !mma; ++nchunk) {
+        const int G = (m + dpt * nchunk - 1) / (dpt * nchunk);
+        if (G > tile_max_groups(tr, dpt)) continue;
+        if ((size_t)tl.max_halo * (G * dpt + 4) * sizeof(float) + rec_smem <= kTileSmem) {
+            chunk = G * dpt;
+            break;
+        }
+    }
+    // automatic choice: staging pays only while the operator records are read
+    // by few chunks; the row-team kernel otherwise
+    if (chunk == 0 || (ctx->opt.apply_kernel == 0 && (m + chunk - 1) / chunk > 2)) return MLPG_OK;
+    ctx->tile_rows = tr;
+    ctx->tile_dpt = dpt;
+    ctx->tile_chunk = chunk;
+    ctx->tile_mma = mma;
+    ctx->tile_xs = mma ? chunk + (16 - chunk % 32 + 32) % 32
+                       : chunk + 4;   // padded shared-memory row: spreads halo rows over the banks
+    ctx->ntile = tl.ntile;
+    ctx->nslot = nslot;
+    cudaStream_t s = ctx->stream;
+    std::vector<int32_t> base32(tl.ntile + 1), hptr32(tl.ntile + 1);
+    for (int64_t t = 0; t <= tl.ntile; ++t) {
+        base32[t] = (int32_t)tl.base[t];
+        hptr32[t] = (int32_t)tl.hptr[t];
+    }
+    MLPG_TRY(dalloc(ctx, &ctx->t_base, tl.ntile + 1));
+    MLPG_TRY(dalloc(ctx, &ctx->t_width, tl.ntile));
+    MLPG_TRY(dalloc(ctx, &ctx->t_row, tl.ntile * tr));
+    MLPG_TRY(dalloc(ctx, &ctx->t_hptr, tl.ntile + 1));
+    MLPG_TRY(dalloc(ctx, &ctx->t_hcol, tl.hcol.size()));
+    MLPG_TRY(dalloc(ctx, &ctx->t_perm, nslot));
+    MLPG_TRY(dalloc(ctx, &ctx->t_lcol, nslot));
+    MLPG_TRY(dalloc(ctx, &ctx->t_rec, nslot * rec_words<D>()));
+    CU(ctx, cudaMemcpyAsync(ctx->t_base, base32.data(), base32.size() * 4, cudaMemcpyHostToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->t_width, tl.width.data(), tl.width.size() * 4, cudaMemcpyHostToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->t_row, tl.row.data(), tl.row.size() * 4, cudaMemcpyHostToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->t_hptr, hptr32.data(), hptr32.size() * 4, cudaMemcpyHostToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->t_hcol, tl.hcol.data(), tl.hcol.size() * 4, cudaMemcpyHostToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->t_perm, tl.perm.data(), nslot * 4, cudaMemcpyHostToDevice, s));
+    CU(ctx, cudaMemcpyAsync(ctx->t_lcol, tl.lcol.data(), nslot * 4, cudaMemcpyHostToDevice, s));
+    // halo offset (index x shared-memory row stride) of every boundary-segment entry's column
+    {
+        std::vector<int32_t> bptr(ctx->n + 1), bcol(std::max<int64_t>(ctx->nb, 1)), bhalo(std::max<int64_t>(ctx->nb, 1), 0);
+        CU(ctx, cudaMemcpyAsync(bptr.data(), ctx->bptr, (ctx->n + 1) * 4, cudaMemcpyDeviceToHost, s));
+        if (ctx->nb > 0) CU(ctx, cudaMemcpyAsync(bcol.data(), ctx->bcol, ctx->nb * 4, cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+        for (int64_t r = 0; r < tl.ntile * tr; ++r) {
+            const int32_t i = tl.row[r];
+            if (i < 0) continue;
+            const int64_t t = r / tr;
+            const int32_t *hb = tl.hcol.data() + tl.hptr[t], *he = tl.hcol.data() + tl.hptr[t + 1];
+            for (int32_t q = bptr[i]; q < bptr[i + 1]; ++q) {
+                const int32_t *hit = std::lower_bound(hb, he, bcol[q]);
+                if (hit == he || *hit != bcol[q]) return set_err(ctx, MLPG_ERR_ARG, "boundary entry outside its tile's halo");
+                bhalo[q] = (int32_t)(hit - hb) * ctx->tile_xs;
+            }
+        }
+        MLPG_TRY(dalloc(ctx, &ctx->t_bhalo, bhalo.size()));
+        CU(ctx, cudaMemcpyAsync(ctx->t_bhalo, bhalo.data(), bhalo.size() * 4, cudaMemcpyHostToDevice, s));
+        CU(ctx, cudaStreamSynchronize(s));
+    }
+    CU(ctx, cudaStreamSynchronize(s));   // the host vectors go out of scope
+    if (mma) {
+        mlpg_status st = MLPG_OK;
+        auto set = [&]() -> mlpg_status {
+            if (tr == 32) { MMA_NT_SWITCH(D, 32, mma_attr, ctx) }
+            MMA_NT_SWITCH(D, 64, mma_attr, ctx)
+        };
+        st = set();
+        if (st != MLPG_OK) return st;
+    } else switch (dpt * 100 + tr) {
+        case 832: MLPG_TRY((tile_attr<D, 8, 32>(ctx))); break;
+        case 864: MLPG_TRY((tile_attr<D, 8, 64>(ctx))); break;
+        case 432: MLPG_TRY((tile_attr<D, 4, 32>(ctx))); break;
+        default: MLPG_TRY((tile_attr<D, 4, 64>(ctx))); break;
+    }
+    ctx->tile_xs_f4 = (int)(tl.max_halo * ctx->tile_xs / 4);
+    ctx->tile_smem = (size_t)ctx->tile_xs_f4 * sizeof(float4) + rec_smem;
+    ctx->tile_max_halo = tl.max_halo;
+    return MLPG_OK;
+}
 
 template <int D>
 static mlpg_status init_operator_storage_d(mlpg_ctx *ctx) {
@@ -900,6 +1618,7 @@ static mlpg_status init_operator_storage_d(mlpg_ctx *ctx) {
     ctx->nbrow = nbr;
     k_coef<D><<<(m + 127) / 128, 128, 0, s>>>(m, ctx->omega, ctx->coef, ctx->fcoef, ctx->coef32);
     CU_LAUNCH(ctx);
+    if (ctx->opt.precision == MLPG_MIXED) MLPG_TRY(init_tiles<D>(ctx));
     return MLPG_OK;
 }
 
@@ -917,6 +1636,11 @@ static mlpg_status form_operators_d(mlpg_ctx *ctx, double kappa) {
     k_form_arrays<D><<<(nnz + 255) / 256, 256, 0, s>>>(nnz, kappa, ctx->rowidx, ctx->tau, ctx->mats,
                                                     ctx->A64, ctx->A32, ctx->T64, ctx->S64);
     CU_LAUNCH(ctx);
+    if (ctx->t_rec) {
+        k_tile_records<D><<<(ctx->nslot + 255) / 256, 256, 0, s>>>(ctx->nslot, nnz, ctx->tile_xs, ctx->t_perm, ctx->t_lcol,
+                                                                   ctx->A32, reinterpret_cast<float4 *>(ctx->t_rec));
+        CU_LAUNCH(ctx);
+    }
     int64_t tot = nnz * m;
     k_materialize<D><<<(tot + 255) / 256, 256, 0, s>>>(nnz, m, ctx->A64, Sf, ctx->coef, ctx->fcoef, ctx->L64);
     CU_LAUNCH(ctx);
@@ -950,7 +1674,52 @@ static mlpg_status form_operators_d(mlpg_ctx *ctx, double kappa) {
 }
 
 mlpg_status form_operators(mlpg_ctx *ctx, double kappa) {
-    return ctx->dim == 3 ? form_operators_d<3>(ctx, kappa) : form_operators_d<2>(ctx, kappa);
+    MLPG_TRY(ctx->dim == 3 ? form_operators_d<3>(ctx, kappa) : form_operators_d<2>(ctx, kappa));
+    if (ctx->opt.outer_precond == 1) MLPG_TRY(form_diffusion(ctx, kappa));
+    return MLPG_OK;
+}
+
+mlpg_status form_diffusion(mlpg_ctx *ctx, double kappa) {
+    const int64_t n = ctx->n;
+    cudaStream_t s = ctx->stream;
+    if (!ctx->Cdiff) {
+        MLPG_TRY(dalloc(ctx, &ctx->Cdiff, ctx->nnz));
+        MLPG_TRY(dalloc(ctx, &ctx->Cinv, (size_t)ctx->nblk * kB * kB));
+        MLPG_TRY(dalloc(ctx, &ctx->dsa_buf, 2 * n));
+    }
+    if (ctx->dim == 3)
+        k_diff_values<3><<<(n + 255) / 256, 256, 0, s>>>(n, ctx->nnz, kappa, ctx->rowptr, ctx->mats, ctx->Cdiff);
+    else
+        k_diff_values<2><<<(n + 255) / 256, 256, 0, s>>>(n, ctx->nnz, kappa, ctx->rowptr, ctx->mats, ctx->Cdiff);
+    CU_LAUNCH(ctx);
+    CU(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+    k_block_inv64<<<(unsigned)((ctx->nblk + 7) / 8), 256, 0, s>>>(ctx->nblk, ctx->rowptr, ctx->col, ctx->Cdiff,
+                                                                 ctx->bmember, ctx->bof, ctx->Cinv, ctx->d_flag);
+    CU_LAUNCH(ctx);
+    int flag = 0;
+    CU(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    if (flag & 64) return set_err(ctx, MLPG_ERR_ARG, "singular diagonal block in the diffusion operator");
+    return MLPG_OK;
+}
+
+mlpg_status apply_C(mlpg_ctx *ctx, const double *X, const double *B, double *Y) {
+    k_csr_spmv64<<<(ctx->n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n, ctx->rowptr, ctx->col, ctx->Cdiff, X, B, Y);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status apply_Ms_scalar(mlpg_ctx *ctx, const double *X, double *Y) {
+    k_csr_spmv64<<<(ctx->n + 255) / 256, 256, 0, ctx->stream>>>(ctx->n, ctx->rowptr, ctx->col,
+                                                                 ctx->mats + 2 * ctx->nnz, X, nullptr, Y);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
+}
+
+mlpg_status apply_Cprec(mlpg_ctx *ctx, double *v, double *z, const double *sc) {
+    k_bjacobi64_vec<<<(unsigned)ctx->nblk, kB, 0, ctx->stream>>>(ctx->nblk, ctx->bmember, ctx->Cinv, v, sc, z);
+    CU_LAUNCH(ctx);
+    return MLPG_OK;
 }
 
 // Device time of each batched L-apply: event pairs from a pool, harvested
@@ -979,11 +1748,19 @@ mlpg_status apply_L64_res(mlpg_ctx *ctx, const double *X, const double *B, doubl
 }
 
 template <int DIM>
+static mlpg_status apply_faces32(mlpg_ctx *ctx, const Team &tm, const float *X, const float *B, float *Y);
+
+template <int DIM>
 static mlpg_status apply_L32_res_d(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
     Team tm = pick_team(ctx->m);
     int64_t grid = team_grid(ctx->n, tm);
     cudaStream_t s = ctx->stream;
     timing_begin(ctx);
+    if (ctx->t_rec) {   // the face terms are added inside the tile kernel
+        MLPG_TRY(run_tile<DIM>(ctx, X, B, Y));
+        timing_end(ctx);
+        return MLPG_OK;
+    }
     grid = rowteam_grid(ctx->n, tm);
     const bool small = ctx->n * (int64_t)ctx->m < (int64_t(1) << 31);
     const bool exact = (tm.dpl << tm.tm_log2) == ctx->m;
@@ -1003,6 +1780,15 @@ static mlpg_status apply_L32_res_d(mlpg_ctx *ctx, const float *X, const float *B
             break;
     }
     CU_LAUNCH(ctx);
+#undef SPMM32_CASE
+#undef SPMM32_ARGS
+    return apply_faces32<DIM>(ctx, tm, X, B, Y);
+}
+
+// the outflow-face pass after either FP32 apply kernel, then the timing event
+template <int DIM>
+static mlpg_status apply_faces32(mlpg_ctx *ctx, const Team &tm, const float *X, const float *B, float *Y) {
+    cudaStream_t s = ctx->stream;
     if (ctx->nbrow > 0) {
         int64_t gb = team_grid(ctx->nbrow, tm);
         float sign = B ? -1.0f : 1.0f;
@@ -1017,11 +1803,9 @@ static mlpg_status apply_L32_res_d(mlpg_ctx *ctx, const float *X, const float *B
                                                        ctx->bcol, ctx->bval32, ctx->coef32, X, sign, Y); break;
         }
 #undef FACE_CASE
+        CU_LAUNCH(ctx);
     }
-#undef SPMM32_CASE
-#undef SPMM32_ARGS
     timing_end(ctx);
-    CU_LAUNCH(ctx);
     return MLPG_OK;
 }
 
@@ -1134,9 +1918,11 @@ mlpg_status build_blocks(mlpg_ctx *ctx) {
     std::sort(key.begin(), key.end());
     ctx->nblk = (n + kB - 1) / kB;
     std::vector<int32_t> member(ctx->nblk * kB, -1), bof(n);
+    ctx->h_order.resize(n);
     for (int64_t r = 0; r < n; ++r) {
         member[r] = key[r].second;
         bof[key[r].second] = (int32_t)r;
+        ctx->h_order[r] = key[r].second;
     }
     MLPG_TRY(dalloc(ctx, &ctx->bmember, ctx->nblk * kB));
     MLPG_TRY(dalloc(ctx, &ctx->bof, n));
