@@ -49,6 +49,9 @@ def _args():
                          "workload, timed per launch (used for kernel profiles)")
     ap.add_argument("--be-steps", type=int, default=None,
                     help="backward-Euler steps per solve (default: the workload's 20; profiling runs use fewer)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra measurements (3D apply, serving stream, batched problems)")
+    ap.add_argument("--no-tune", action="store_true", help="default tile shape instead of the autotuned one")
     return ap.parse_args()
 
 
@@ -244,10 +247,131 @@ def _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank):
         print(json.dumps({"metric": "batched L-apply", "value": us, "unit": "us/launch", "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
                           "dtype": "f32" if prec == pkg.MLPG_MIXED else "f64",
-                          "config": {"workload": WORKLOAD, "mode": "apply"},
+                          "config": {"workload": WORKLOAD, "mode": "apply",
+                                     "apply_kernel": st["apply_kernel"], "tile_chunk": st["tile_chunk"],
+                                     "options": {k: opts.get(k) for k in ("apply_kernel", "tile_rows", "tile_dpt")}},
                           "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                        "frac": gbs / hbm, "peak_kind": kind,
                                        "bytes_per_launch": st["spmm_bytes"]}}))
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "two_region_256_phi.npz")
+
+
+def _golden():
+    """The oracle's scalar flux of the full workload (written by
+    tests/golden/make_two_region_256_golden.py), or None."""
+    try:
+        return np.load(GOLDEN)
+    except OSError:
+        return None
+
+
+def _oracle_counts(side=24, steps=2):
+    """The oracle's own inner scheme (GMRES + ILUT per direction, the paper's
+    Sec. 4.2 solver) on a sample of the workload: iterations per inner solve
+    and outer iterations per step."""
+    import oracle.mlpg_oracle as O
+    import mlpg_inputs as mi
+    prob = mi.two_region_2d(n_per_dim=side, steps=steps)
+    disc = O.Discretization(prob.x, prob.R, prob.lo, prob.hi)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    tr = O.Transport(disc, F, prob.omega, prob.w, psi_b=prob.inflow)
+    sol = O.Solver(tr, outer_tol=1e-12, inner="ilut-gmres", inner_tol=1e-12)
+    _, _, st = sol.run(np.zeros((tr.M, disc.n)), prob.dt, prob.steps)
+    c = [k for k in sol.inner_counts if k > 0]
+    return {"sample": f"{side}x{side} points, {steps} steps, inner GMRES(50) + ILUT(1e-4, fill 10) to 1e-12, "
+                      f"outer GMRES to 1e-12",
+            "inner_per_solve": float(np.mean(c)) if c else 0.0,
+            "outer_per_step": float(np.mean([x.outer_iterations for x in st]))}
+
+
+def _apply_3d(pkg, stream):
+    """Batched FP32 L-apply of the 3D configuration (40^3 points, the Alg. 2
+    set refined within 15 degrees of +x: 272 directions), automatic kernel
+    choice; algorithmic bytes per launch over the median event time."""
+    import mlpg_inputs as mi
+    from paper_2008_02205_gb300 import autotune
+    prob = mi.lognormal_3d(refine=(1, 5, 15.0))
+    us, st = autotune.time_apply(prob, {}, reps=10, warmup=3, stream=stream)
+    hbm, kind = _peaks()
+    gbs = st["spmm_bytes"] / (us * 1e-6) / 1e9
+    return {"workload": "3d-lognormal-40^3-refined272", "us_per_launch": us, "bytes_per_launch": st["spmm_bytes"],
+            "achieved_gbs": gbs, "frac": gbs / hbm, "peak": hbm, "peak_kind": kind,
+            "kernel": "row tiles" if st["apply_kernel"] == 2 else "row teams", "nnz": st["nnz"]}
+
+
+def _serving(pkg, count=10, rates=(2.0, 8.0)):
+    """The serving configuration on a bounded sample: a Poisson stream of 2D
+    and 3D requests (4k-64k points here, 12-272 directions, two-region
+    sigma_t, 5-20 steps), admitted by estimated device memory, continuous
+    batching; p50/p99 latency from arrival and solves/s at two arrival
+    rates, against the same requests solved one after another in FP64."""
+    import time as _t
+    import mlpg_inputs as mi
+    from paper_2008_02205_gb300.serving import Request, Server, latency_percentiles
+    out = {"requests": count, "n_range": [4096, 65536], "steps_range": [5, 20], "budget_gb": 96, "rates": []}
+    mixed = dict(precision=pkg.MLPG_MIXED)
+    for rate in rates:
+        stream = mi.serving_stream(count=count, rate=rate, seed=5000, n_range=(4096, 65536), steps_range=(5, 20))
+        reqs = [Request(p, p.steps, p.dt, arrival=t, options=mixed) for p, t in stream]
+        srv = Server(hbm_budget_bytes=96 << 30, max_active=8)
+        t0 = _t.perf_counter()
+        res = srv.run(reqs)
+        wall = _t.perf_counter() - t0
+        ok = [r for r in res if r.error is None]
+        lat = latency_percentiles(res)
+        out["rates"].append({"rate_per_s": rate, "solves_per_s": len(ok) / wall, "wall_s": wall,
+                             "p50_s": lat.get("p50"), "p99_s": lat.get("p99"), "failed": len(res) - len(ok),
+                             "peak_active": srv.peak_active, "steps_during_setup": srv.steps_during_open})
+    # the same requests, one after another, plain FP64
+    stream = mi.serving_stream(count=count, rate=rates[0], seed=5000, n_range=(4096, 65536), steps_range=(5, 20))
+    t0 = _t.perf_counter()
+    for p, _ in stream:
+        with pkg.TransportProblem.from_problem(p, precision=pkg.MLPG_FP64) as tp:
+            tp.integrate().assemble()
+            tp.run(p.dt, p.steps)
+    seq = _t.perf_counter() - t0
+    out["fp64_sequential"] = {"solves_per_s": count / seq, "wall_s": seq}
+    return out
+
+
+def _batched(pkg, count=64, steps=10):
+    """The batched configuration: 64 independent 2D problems (1k-64k points,
+    S4-S12, sigma_t in [0.1, 10], scattering ratio in [0, 0.99]), mixed
+    precision, every problem advanced by one concurrent batched step per
+    time step; against the same problems stepped one after another."""
+    import time as _t
+    import mlpg_inputs as mi
+    probs = mi.batched_2d(count, steps=steps)
+    tps = []
+    try:
+        for p in probs:
+            tps.append(pkg.TransportProblem.from_problem(p, precision=pkg.MLPG_MIXED))
+            tps[-1].integrate().assemble()
+        pkg.TransportProblem.step_batch(tps, probs[0].dt)          # operators formed, buffers made
+        for tp in tps:
+            tp.set_state(np.zeros((tp.n, tp.m)))
+        t0 = _t.perf_counter()
+        for _ in range(steps):
+            pkg.TransportProblem.step_batch(tps, probs[0].dt)
+        for tp in tps:
+            tp.scalar_flux()
+        batched = _t.perf_counter() - t0
+        for tp in tps:
+            tp.set_state(np.zeros((tp.n, tp.m)))
+        t0 = _t.perf_counter()
+        for tp in tps:
+            for _ in range(steps):
+                tp.step(probs[0].dt)
+            tp.scalar_flux()
+        seq = _t.perf_counter() - t0
+    finally:
+        for tp in tps:
+            tp.close()
+    return {"problems": count, "steps": steps, "points": int(sum(p.n for p in probs)),
+            "solves_per_s": count / batched, "wall_s": batched,
+            "sequential": {"solves_per_s": count / seq, "wall_s": seq}}
 
 
 def main():
@@ -274,6 +398,11 @@ def main():
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     opts = dict(precision=prec, stream=stream.cuda_stream)
+    tuned = None
+    if prec == pkg.MLPG_MIXED and not args.no_tune:
+        from paper_2008_02205_gb300 import autotune
+        tuned = autotune.tuned_options(prob, stream=stream)   # times each tile shape once, then cached
+        opts.update(tuned)
     host = dict(x=prob.x, R=prob.R, om=prob.omega, w=prob.w, st=prob.sigma_t, ss=prob.sigma_s, q=prob.q)
     dv = {k: torch.tensor(v, dtype=torch.float64, device=dev) for k, v in host.items()}
     flux = torch.empty(prob.n, dtype=torch.float64, device=dev)
@@ -358,6 +487,27 @@ def main():
         phi_mixed = phi_host if e2e_times else flux.cpu().numpy()
         err = float(np.linalg.norm(phi_mixed - phi64) / np.linalg.norm(phi64))
         fp64_info = {"solves_per_s": 1.0 / t64, "rel_l2_vs_fp64": err}
+    # error against the oracle's solve of the same workload (stored by an oracle-only script)
+    oracle_err = None
+    g = _golden()
+    if g is not None and args.n == 256 and prob.steps == 20:
+        ref = g["phi_20"]
+        phi_m = phi_host if e2e_times else flux.cpu().numpy()
+        oracle_err = {"rel_l2_vs_oracle": float(np.linalg.norm(phi_m - ref) / np.linalg.norm(ref)),
+                      "oracle_outer_per_step": float(np.mean(g["outer_iterations"]))}
+        if fp64_info is not None:
+            fp64_info["rel_l2_vs_oracle"] = float(np.linalg.norm(phi64 - ref) / np.linalg.norm(ref))
+    extras = {}
+    if not args.no_extras and rank == 0 and world == 1:
+        for name, fn in (("apply_3d", lambda: _apply_3d(pkg, stream)), ("serving", lambda: _serving(pkg)),
+                         ("batched", lambda: _batched(pkg))):
+            try:
+                extras[name] = fn()
+            except Exception as e:      # an extra measurement never hides the main line
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
+    counts = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        counts = _oracle_counts()
     hbm, peak_kind = _peaks()
     roof = None
     if spmm_launch > 0 and spmm_ms > 0:
@@ -382,8 +532,15 @@ def main():
                            "inner_last_step": stats["last_inner_iters"],
                            "inner_solves_last_step": stats["last_inner_solves"],
                            "refinements_last_step": stats["last_refinements"],
-                           "outer_total": stats["total_outer_iters"], "inner_total": stats["total_inner_iters"]},
+                           "outer_total": stats["total_outer_iters"], "inner_total": stats["total_inner_iters"],
+                           "gpu_inner_per_direction_solve_last_step": stats["last_inner_iters"] / max(
+                               1, prob.m * stats["last_inner_solves"]),
+                           "oracle_outer_per_step_full_size": (oracle_err or {}).get("oracle_outer_per_step"),
+                           "oracle_ilut_gmres": counts},
             "fp64_path": fp64_info,
+            "oracle": oracle_err,
+            "apply_tiles": tuned,
+            "extras": extras,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(prob.n * 8)},
             "roofline": roof, "clocks": clk, "gpu_launches": launches,
