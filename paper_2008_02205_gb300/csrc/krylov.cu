@@ -582,7 +582,11 @@ __global__ void k_extrap(int64_t N, double a, double b, double c, double *__rest
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= N) return;
     const double p = psi[e];
-    psi[e] = a * p + b * h1[e] + c * h2[e];
+    // a history entry with a zero weight is not read: it may not hold a state yet
+    double v = a * p;
+    if (b != 0.0) v += b * h1[e];
+    if (c != 0.0) v += c * h2[e];
+    psi[e] = v;
     h2[e] = p;
 }
 
@@ -1058,6 +1062,8 @@ static mlpg_status ensure_history(mlpg_ctx *ctx) {
         const size_t N = (size_t)ctx->n * ctx->m;
         MLPG_TRY(dalloc(ctx, &ctx->hist[0], N));
         MLPG_TRY(dalloc(ctx, &ctx->hist[1], N));
+        CU(ctx, cudaMemsetAsync(ctx->hist[0], 0, sizeof(double) * N, ctx->stream));
+        CU(ctx, cudaMemsetAsync(ctx->hist[1], 0, sizeof(double) * N, ctx->stream));
         ctx->nhist = 0;
     }
     return MLPG_OK;
