@@ -136,7 +136,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-PROFILE = os.path.join(ROOT, "profiles", "k_spmm32-2d-two-region-256x256-S8.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_spmm32_tile-2d-two-region-256x256-S8.md")
+APPLY_KERNELS = {1: "k_spmm32 (row teams)", 2: "k_spmm32_tile (row tiles, TMA-staged)",
+                 3: "k_spmm32_mma (row tiles, tensor cores)"}
 KERNEL_SRC = os.path.join(ROOT, "paper_2008_02205_gb300", "csrc", "operators.cu")
 
 
@@ -513,9 +515,11 @@ def main():
     if spmm_launch > 0 and spmm_ms > 0:
         per_launch_s = spmm_ms / spmm_launch / 1e3
         achieved = stats["spmm_bytes"] / per_launch_s / 1e9
-        roof = {"kernel": "k_spmm32 (batched L-apply)" if prec == pkg.MLPG_MIXED else "k_spmm64 (batched L-apply)",
+        roof = {"kernel": (APPLY_KERNELS.get(stats["apply_kernel"], "k_spmm32") if prec == pkg.MLPG_MIXED
+                           else "k_spmm64") + ": batched L-apply",
                 "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": _traffic() if prec == pkg.MLPG_MIXED else None, "peak_kind": peak_kind,
+                "traffic": _traffic() if prec == pkg.MLPG_MIXED and stats["apply_kernel"] == 2 else None,
+                "peak_kind": peak_kind,
                 "bytes_per_launch": stats["spmm_bytes"], "us_per_launch": per_launch_s * 1e6}
     lat = sorted(per)
     p50 = lat[len(lat) // 2]

@@ -202,6 +202,7 @@ struct mlpg_ctx {
     size_t tile_smem = 0;       // dynamic shared memory of the tiled kernel: halo rows + record stages
     int tile_xs_f4 = 0;         // float4 words of the staged halo (the record stages follow)
     int64_t tile_max_halo = 0;  // largest halo of a tile
+    int *d_tile_err = nullptr;  // set by a tile-kernel wait that gave up (bounded waits)
     int32_t *t_base = nullptr, *t_width = nullptr, *t_row = nullptr, *t_hptr = nullptr, *t_hcol = nullptr;
     int32_t *t_perm = nullptr, *t_lcol = nullptr;
     int32_t *t_bhalo = nullptr;  // [nb]: halo offset (index x tile_xs) of each boundary-segment entry's column
@@ -247,6 +248,7 @@ mlpg_status dalloc(mlpg_ctx *ctx, T **p, size_t count) {
 // kernels / launchers (neighbors.cu, assemble.cu, operators.cu, krylov.cu)
 mlpg_status run_neighbors(mlpg_ctx *ctx);
 mlpg_status run_cells_2d(mlpg_ctx *ctx, int tri_points, int line_points);
+mlpg_status run_cells_3d(mlpg_ctx *ctx);   // cells3d.cu: element lists and volumes on the device
 mlpg_status run_interp(mlpg_ctx *ctx);
 mlpg_status run_assemble(mlpg_ctx *ctx);
 mlpg_status run_interp_3d(mlpg_ctx *ctx);

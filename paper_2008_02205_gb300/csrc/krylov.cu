@@ -4,14 +4,19 @@
 // layout v[i][m] (system index fastest).  Each system has its own Hessenberg
 // matrix, Givens rotations, residual estimate and convergence mask, all kept
 // on the device; the host only polls the number of systems still iterating
-// every few Arnoldi steps.  Orthogonalisation is classical Gram-Schmidt applied
-// twice (CGS2); dot products are accumulated in FP64 whatever the vector type.
-// Right preconditioning by the inverse diagonal (Jacobi) of each L_m.
+// every few Arnoldi steps.  Orthogonalisation is classical Gram-Schmidt
+// applied twice (CGS2) in FP64, or once in the FP32 correction solves (16-byte
+// vectorised passes); block sums are formed in FP64 whatever the vector type.
+// Right preconditioning by the block-Jacobi inverses (16-point Morton blocks)
+// of each L_m.
 //
-// The same engine with M = 1 and no preconditioner runs the scattering
-// iteration on the scalar-flux coefficients, Eq. krylov-operator:
+// The same engine with M = 1 runs the scattering iteration on the
+// scalar-flux coefficients, Eq. krylov-operator:
 //   (I - D L^{-1} MS) Phi = D L^{-1} (T Psi^{n-1} + r),
-// whose operator apply is one batched transport solve (all directions).
+// whose operator apply is one batched transport solve (all directions); it is
+// unpreconditioned (the paper's) or right-preconditioned by the DSA-like
+// diffusion correction (flexible GMRES), and with M = 1 it also solves the
+// diffusion systems of that correction.
 #include <algorithm>
 #include <cmath>
 #include <functional>
@@ -1090,7 +1095,13 @@ static mlpg_status prepare_step(mlpg_ctx *ctx, double dt) {
     return MLPG_OK;
 }
 
-static void finish_step_stats(mlpg_ctx *ctx) {
+static mlpg_status finish_step_stats(mlpg_ctx *ctx) {
+    if (ctx->d_tile_err) {   // a bounded wait of the tile kernel gave up during this step
+        int terr = 0;
+        CU(ctx, cudaMemcpyAsync(&terr, ctx->d_tile_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        if (terr) return set_err(ctx, MLPG_ERR_CUDA, "a copy into the tile kernel's shared memory timed out");
+    }
     long long its[3] = {0, 0, 0};
     if (cudaMemcpyAsync(its, ctx->d_its, sizeof(its), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
         cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
@@ -1103,6 +1114,7 @@ static void finish_step_stats(mlpg_ctx *ctx) {
     ctx->st.total_outer_iters += ctx->st.last_outer_iters;
     ctx->st.total_inner_iters += ctx->st.last_inner_iters;
     ctx->st.total_dsa_iters += ctx->st.last_dsa_iters;
+    return MLPG_OK;
 }
 
 mlpg_status step_fp64(mlpg_ctx *ctx, double dt) {
@@ -1125,8 +1137,7 @@ mlpg_status step_fp64(mlpg_ctx *ctx, double dt) {
     CU(ctx, cudaStreamSynchronize(s));
     MLPG_TRY(shard_sum_host(ctx, ctx->h_red, 2));
     ctx->st.last_residual = ctx->h_red[1] > 0 ? std::sqrt(ctx->h_red[0] / ctx->h_red[1]) : 0.0;
-    finish_step_stats(ctx);
-    return MLPG_OK;
+    return finish_step_stats(ctx);
 }
 
 mlpg_status step_mixed(mlpg_ctx *ctx, double dt) {
@@ -1185,8 +1196,7 @@ mlpg_status step_mixed(mlpg_ctx *ctx, double dt) {
     MLPG_TRY(shard_sum_dev(ctx, ctx->Phi, n));
     ctx->st.last_refinements = k;
     ctx->st.last_residual = rel;
-    finish_step_stats(ctx);
-    return MLPG_OK;
+    return finish_step_stats(ctx);
 }
 
 }  // namespace mlpg

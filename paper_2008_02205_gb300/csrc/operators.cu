@@ -310,14 +310,16 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
                                                 float *__restrict__ Y) {
     constexpr int K = NA<D>();
     const int TM = 1 << tm_log2;
-    const int lane = threadIdx.x & (TM - 1);
+    // grid y: chunks of TM x DPL directions (one chunk when the team covers all m)
+    const int m0 = blockIdx.y * (TM * DPL), lane = threadIdx.x & (TM - 1);
+    const int ml = m0 + lane;   // this lane's first direction
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> tm_log2;
     if (row >= n) return;
     float c[K][DPL], acc[DPL];
     bool on[DPL];
 #pragma unroll
     for (int t = 0; t < DPL; ++t) {
-        int k = lane + t * TM;
+        int k = m0 + lane + t * TM;
         on[t] = EXACT || k < m;
         k = on[t] ? k : m - 1;
 #pragma unroll
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
     int32_t p = rowptr[row];
     if constexpr (K == 6) {   // 2D: the six values in named registers (schedules best)
         for (; p + 1 < p1; p += 2) {   // two entries in flight
-            const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)lane, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)lane;
+            const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)ml, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)ml;
             const float a0 = A32[p], a1 = A32[nnz + p], a2 = A32[2 * nnz + p], a3 = A32[3 * nnz + p],
                         a4 = A32[4 * nnz + p], a5 = A32[5 * nnz + p];
             const float b0 = A32[p + 1], b1 = A32[nnz + p + 1], b2 = A32[2 * nnz + p + 1],
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
         }
     }
     for (; p + 1 < p1; p += 2) {   // two entries in flight (generic number of arrays)
-        const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)lane, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)lane;
+        const IDX jb0 = (IDX)col[p] * (IDX)m + (IDX)ml, jb1 = (IDX)col[p + 1] * (IDX)m + (IDX)ml;
         float a[K], b[K];
 #pragma unroll
         for (int q = 0; q < K; ++q) {
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
         }
     }
     for (; p < p1; ++p) {
-        const IDX jb = (IDX)col[p] * (IDX)m + (IDX)lane;
+        const IDX jb = (IDX)col[p] * (IDX)m + (IDX)ml;
         float a[K];
 #pragma unroll
         for (int q = 0; q < K; ++q) a[q] = A32[q * nnz + p];
@@ -381,7 +383,7 @@ __global__ void __launch_bounds__(256) k_spmm32(int64_t n, int m, int tm_log2, i
             }
         }
     }
-    const IDX rb = (IDX)row * (IDX)m + (IDX)lane;
+    const IDX rb = (IDX)row * (IDX)m + (IDX)ml;
 #pragma unroll
     for (int t = 0; t < DPL; ++t) {
         if (on[t]) {
@@ -442,18 +444,15 @@ __global__ void __launch_bounds__(256) k_faces32(int64_t nbr, int m, int tm_log2
 }
 
 // ---------------------------------------------------------------------------
-// Tiled FP32 L-apply (m % 4 == 0).  One CTA per (row tile, direction chunk):
-//   1. the tile's halo rows of X (the union of its rows' columns, mc of the m
-//      directions) are copied into shared memory once with 16-byte cp.async;
-//   2. thread (s, g) owns row slot s of the tile and DPT directions of the
-//      chunk (quads g and g + G, G = mc / DPT, so that the threads of one row
-//      read one contiguous run of the staged row); it walks the tile's
-//      sliced-ELL records (the K base-array values of an entry and its halo
-//      index; the rows of a warp read adjacent records), combines the K values
-//      with its directions' coefficients and accumulates value x X from shared
-//      memory, two directions per packed FP32 FMA;
-//   3. Y = L X, or Y = B - L X, is written for its row and directions.
-// The outflow-face terms of the boundary rows are added by k_faces32.
+// Row tiles (m % 4 == 0), shared by the CUDA-core and tensor-core tile
+// kernels.  A tile is TR Morton-consecutive rows; its halo is the sorted union
+// of their columns.  One CTA per (row tile, direction chunk) stages the halo
+// rows of X (mc of the m directions) in shared memory once, so a neighbour
+// row shared by several rows of the tile is read from HBM once per tile.  The
+// tile's entries are sliced-ELL records, entry k of row slot s at
+// [k][s] (width padded to a multiple of kRecK with zero records): the K
+// base-array values of the entry and the offset of its column's staged row,
+// padded to whole float4 words.
 // ---------------------------------------------------------------------------
 template <int D>
 __host__ __device__ constexpr int rec_words() { return (NA<D>() + 4) / 4 * 4; }   // K values + halo index, padded to float4
@@ -511,41 +510,88 @@ __device__ __forceinline__ void stage_records(float4 *Rs, int buf, const float4 
     }
 }
 
+// ---- bulk copies (the TMA engine) completed on mbarriers, bounded waits -----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// one arrival that also expects `bytes` of copies on the barrier's current phase
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// true once the barrier's phase of this parity has completed; false after 2^16
+// tries (each try waits for a while in hardware), so that no wait is endless
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (int it = 0; it < (1 << 16); ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Tiled FP32 L-apply, one CTA per (row tile, direction chunk).  Thread 0
+// feeds the CTA's shared memory through bulk copies (the TMA engine), each
+// completing on an mbarrier:
+//   * the halo rows of X (the union of the tile's columns, the chunk's
+//     directions): one copy per row, all on one barrier;
+//   * the tile's record slots, kRecK entries per stage, kRecStages stages in
+//     flight; a stage's buffer is refilled once every thread is done with it.
+// Thread (s, g) owns row slot s and DPT directions of the chunk (quads g and
+// g + G, G = mc / DPT, so the threads of a row read one contiguous run of the
+// staged row), combines the K base-array values of an entry with its
+// directions' coefficients and accumulates value x X, two directions per
+// packed FP32 FMA; then it adds the outflow-face terms of a boundary row and
+// writes Y = L X or Y = B - L X.  Every decision taken on a wait is
+// block-uniform; a wait that gives up sets *err, lets the copies in flight
+// land (bounded waits) and ends the CTA.
 template <int D, int DPT, int TR>
 __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
-    int m, int mc, int xs, int xs_f4, const int32_t *__restrict__ base, const int32_t *__restrict__ width,
+    int m, int mc, int xs, int hx_f4, const int32_t *__restrict__ base, const int32_t *__restrict__ width,
     const int32_t *__restrict__ trow, const int32_t *__restrict__ hptr, const int32_t *__restrict__ hcol,
     const float4 *__restrict__ rec, const float *__restrict__ coef32, const int32_t *__restrict__ bptr,
     const int32_t *__restrict__ bhalo, const float *__restrict__ bval, int64_t nb, const float *__restrict__ X,
-    const float *__restrict__ B, float *__restrict__ Y) {
-    constexpr int K = NA<D>(), RW4 = rec_words<D>() / 4, NQ = DPT / 4;
+    const float *__restrict__ B, float *__restrict__ Y, int *__restrict__ err) {
+    constexpr int K = NA<D>(), RW4 = rec_words<D>() / 4, NQ = DPT / 4, NS = kRecStages;
+    constexpr int SF4 = kRecK * TR * RW4;   // float4 per record stage
+    constexpr uint32_t SBYTES = SF4 * 16u;
     extern __shared__ float4 smem_x4[];
+    __shared__ __align__(8) uint64_t bars[NS + 1];   // record stages, then the halo
     float *Xs = reinterpret_cast<float *>(smem_x4);
-    float4 *Rs = smem_x4 + xs_f4;
-    const int t = blockIdx.x;
-    const int m0 = blockIdx.y * mc;
-    const int mcw = min(mc, m - m0);   // directions of this chunk (a multiple of 4)
-    const int G = mc / DPT;
+    float4 *Rs = smem_x4 + hx_f4;
+    const int t = blockIdx.x, m0 = blockIdx.y * mc, mcw = min(mc, m - m0), G = mc / DPT;
     const int s = threadIdx.x / G, g = threadIdx.x - s * G;
-    // 1. stage the halo rows (chunk columns m0 .. m0 + mcw): the first copy
-    //    group.  Thread (s, g) copies quads g, g + G, ... of halo rows s, s + TR, ...
-    {
-        const int h0 = hptr[t], hn = hptr[t + 1] - h0, q4 = mcw >> 2;
-        for (int hh = s; hh < hn; hh += TR) {
-            const float *src = X + (int64_t)hcol[h0 + hh] * m + m0;
-            for (int qq = g; qq < q4; qq += G) cp_async16(Xs + hh * xs + 4 * qq, src + 4 * qq);
-        }
-        cp_async_commit();
-    }
-    // 2. record pipeline prologue: stages 0 .. kRecStages - 2, one copy group each
     const int W = width[t], nst = W / kRecK;
     const float4 *rg = rec + (int64_t)base[t] * RW4;
-#pragma unroll
-    for (int st = 0; st < kRecStages - 1; ++st) {
-        stage_records<D, TR>(Rs, st, rg, st, W);
-        cp_async_commit();
+    const int h0 = hptr[t], hn = hptr[t + 1] - h0;
+    const uint32_t row_bytes = (uint32_t)mcw * 4u;
+    if (threadIdx.x == 0) {
+        for (int b = 0; b <= NS; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    // the thread's directions: quad g and (DPT = 8) quad g + G of the chunk
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect(&bars[NS], (uint32_t)hn * row_bytes);
+        for (int st = 0; st < NS && st < nst; ++st) {
+            mbar_expect(&bars[st], SBYTES);
+            bulk_g2s(Rs + st * SF4, rg + (int64_t)st * SF4, SBYTES, &bars[st]);
+        }
+    }
+    for (int hh = threadIdx.x; hh < hn; hh += blockDim.x)
+        bulk_g2s(Xs + hh * xs, X + (int64_t)hcol[h0 + hh] * m + m0, row_bytes, &bars[NS]);
+    // the thread's directions and their coefficient pairs
     int qoff[NQ];
     bool on[NQ];
 #pragma unroll
@@ -553,7 +599,7 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
         qoff[u] = 4 * (g + u * G);
         on[u] = qoff[u] < mcw;
     }
-    float2 c[K][2 * NQ];   // coefficient pairs of the K - 1 direction-dependent arrays (c[0] unused)
+    float2 c[K][2 * NQ];   // c[0] unused (the coefficient of the first array is 1)
 #pragma unroll
     for (int u = 0; u < NQ; ++u)
 #pragma unroll
@@ -565,25 +611,22 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     float2 acc[2 * NQ];
 #pragma unroll
     for (int j = 0; j < 2 * NQ; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    // 3. the entries, kRecK per stage (tile widths are multiples of kRecK:
-    //    padding slots hold zeros); stage st + kRecStages - 1 is copied while
-    //    st is used
-    for (int st = 0; st < nst; ++st) {
-        cp_async_wait<kRecStages - 2>();   // the halo and stage st have landed
-        __syncthreads();                   // ... for every thread; buffer (st - 1) % kRecStages is free
-        stage_records<D, TR>(Rs, (st + kRecStages - 1) % kRecStages, rg, st + kRecStages - 1, W);
-        cp_async_commit();
-        const float4 *rb = Rs + (st % kRecStages) * rec_stage_f4<D, TR>() + s;
+    bool ok = __syncthreads_and(mbar_wait(&bars[NS], 0));
+    int st = 0;
+    for (; st < nst && ok; ++st) {
+        const int b = st % NS;
+        if (!__syncthreads_and(mbar_wait(&bars[b], (st / NS) & 1))) { ok = false; break; }
+        const float4 *rb = Rs + b * SF4 + s * RW4;
 #pragma unroll
         for (int kk = 0; kk < kRecK; ++kk) {
             float a[4 * RW4];
 #pragma unroll
             for (int q = 0; q < RW4; ++q) {
-                const float4 v = rb[q * (kRecK * TR) + kk * TR];
+                const float4 v = rb[kk * TR * RW4 + q];
                 a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
             }
             const float *xr = Xs + __float_as_int(a[K]);
-            float2 ab[K];                  // the entry's values, each in both halves of a pair
+            float2 ab[K];   // the entry's values, each in both halves of a pair
 #pragma unroll
             for (int k2 = 0; k2 < K; ++k2) ab[k2] = make_float2(a[k2], a[k2]);
 #pragma unroll
@@ -599,12 +642,24 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
                 }
             }
         }
+        __syncthreads();   // every thread is done with buffer b
+        if (threadIdx.x == 0 && st + NS < nst) {
+            mbar_expect(&bars[b], SBYTES);
+            bulk_g2s(Rs + b * SF4, rg + (int64_t)(st + NS) * SF4, SBYTES, &bars[b]);
+        }
     }
-    cp_async_wait<0>();   // no copy outlives the CTA
+    if (!ok) {   // (block-uniform) report, let the copies in flight land, leave
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1);
+            mbar_wait(&bars[NS], 0);
+            for (int k = st; k < nst && k < st + NS; ++k) mbar_wait(&bars[k % NS], (k / NS) & 1);
+        }
+        __syncthreads();
+        return;
+    }
     const int32_t row = trow[(int64_t)t * TR + s];
     if (row < 0) return;
-    // 4. outflow-face terms of a boundary row: sum_f max(Omega . n_f, 0) (S_f X)_i
-    //    over the row's boundary-segment entries, whose columns are in the halo
+    // outflow-face terms of a boundary row: sum_f max(Omega . n_f, 0) (S_f X)_i
     const int32_t q0 = bptr[row], q1 = bptr[row + 1];
     if (q1 > q0) {
         float2 fc[NF<D>()][2 * NQ];
@@ -640,15 +695,14 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
             }
         }
     }
-    // 5. write the row
 #pragma unroll
     for (int u = 0; u < NQ; ++u) {
         if (!on[u]) continue;
         const int64_t e = (int64_t)row * m + m0 + qoff[u];
         float4 o = make_float4(acc[2 * u].x, acc[2 * u].y, acc[2 * u + 1].x, acc[2 * u + 1].y);
         if (B) {
-            const float4 b = *reinterpret_cast<const float4 *>(B + e);
-            o = make_float4(b.x - o.x, b.y - o.y, b.z - o.z, b.w - o.w);
+            const float4 bv = *reinterpret_cast<const float4 *>(B + e);
+            o = make_float4(bv.x - o.x, bv.y - o.y, bv.z - o.z, bv.w - o.w);
         }
         *reinterpret_cast<float4 *>(Y + e) = o;
     }
@@ -1402,7 +1456,7 @@ static mlpg_status launch_tile(mlpg_ctx *ctx, const float *X, const float *B, fl
     k_spmm32_tile<D, DPT, TR><<<tg, threads, ctx->tile_smem, ctx->stream>>>(
         ctx->m, ctx->tile_chunk, ctx->tile_xs, ctx->tile_xs_f4, ctx->t_base, ctx->t_width, ctx->t_row, ctx->t_hptr,
         ctx->t_hcol, reinterpret_cast<const float4 *>(ctx->t_rec), ctx->coef32, ctx->bptr, ctx->t_bhalo, ctx->bval32,
-        ctx->nb, X, B, Y);
+        ctx->nb, X, B, Y, ctx->d_tile_err);
     CU_LAUNCH(ctx);
     return MLPG_OK;
 }
@@ -1557,6 +1611,10 @@ static mlpg_status init_tiles(mlpg_ctx *ctx) {
     ctx->tile_xs_f4 = (int)(tl.max_halo * ctx->tile_xs / 4);
     ctx->tile_smem = (size_t)ctx->tile_xs_f4 * sizeof(float4) + rec_smem;
     ctx->tile_max_halo = tl.max_halo;
+    if (!ctx->d_tile_err) {
+        MLPG_TRY(dalloc(ctx, &ctx->d_tile_err, 1));
+        CU(ctx, cudaMemsetAsync(ctx->d_tile_err, 0, sizeof(int), s));
+    }
     return MLPG_OK;
 }
 
@@ -1761,22 +1819,31 @@ static mlpg_status apply_L32_res_d(mlpg_ctx *ctx, const float *X, const float *B
         timing_end(ctx);
         return MLPG_OK;
     }
-    grid = rowteam_grid(ctx->n, tm);
+    // ten base arrays (3D): at most four directions per lane, the rest in direction chunks
+    // (grid y), so that the coefficient registers leave room for enough warps per SM
+    Team tt = tm;
+    int nchunk = 1;
+    if (DIM == 3 && tm.dpl > 4) {
+        nchunk = (ctx->m + 127) / 128;
+        tt.tm_log2 = 5;
+        tt.dpl = (ctx->m + 32 * nchunk - 1) / (32 * nchunk);
+    }
+    const dim3 tgrid((unsigned)rowteam_grid(ctx->n, tt), (unsigned)nchunk);
     const bool small = ctx->n * (int64_t)ctx->m < (int64_t(1) << 31);
-    const bool exact = (tm.dpl << tm.tm_log2) == ctx->m;
-#define SPMM32_ARGS ctx->n, ctx->m, tm.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->A32, ctx->coef32, X, B, Y
-#define SPMM32_CASE(D)                                                                         \
-    case D:                                                                                    \
-        if (exact && small) k_spmm32<D, true, int32_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS); \
-        else if (small) k_spmm32<D, false, int32_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);    \
-        else k_spmm32<D, false, int64_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);               \
+    const bool exact = nchunk == 1 && (tt.dpl << tt.tm_log2) == ctx->m;
+#define SPMM32_ARGS ctx->n, ctx->m, tt.tm_log2, ctx->nnz, ctx->rowptr, ctx->col, ctx->A32, ctx->coef32, X, B, Y
+#define SPMM32_CASE(D)                                                                          \
+    case D:                                                                                     \
+        if (exact && small) k_spmm32<D, true, int32_t, DIM><<<tgrid, 256, 0, s>>>(SPMM32_ARGS); \
+        else if (small) k_spmm32<D, false, int32_t, DIM><<<tgrid, 256, 0, s>>>(SPMM32_ARGS);    \
+        else k_spmm32<D, false, int64_t, DIM><<<tgrid, 256, 0, s>>>(SPMM32_ARGS);               \
         break;
-    switch (tm.dpl) {
+    switch (tt.dpl) {
         SPMM32_CASE(1) SPMM32_CASE(2) SPMM32_CASE(3) SPMM32_CASE(4) SPMM32_CASE(5) SPMM32_CASE(6)
         SPMM32_CASE(7) SPMM32_CASE(8) SPMM32_CASE(9) SPMM32_CASE(10) SPMM32_CASE(11) SPMM32_CASE(12)
         default:
-            if (small) k_spmm32<16, false, int32_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);
-            else k_spmm32<16, false, int64_t, DIM><<<grid, 256, 0, s>>>(SPMM32_ARGS);
+            if (small) k_spmm32<16, false, int32_t, DIM><<<tgrid, 256, 0, s>>>(SPMM32_ARGS);
+            else k_spmm32<16, false, int64_t, DIM><<<tgrid, 256, 0, s>>>(SPMM32_ARGS);
             break;
     }
     CU_LAUNCH(ctx);
