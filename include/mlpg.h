@@ -98,6 +98,8 @@ typedef struct {
     double dsa_tol;        /* outer_precond 1: tolerance of the FP64 diffusion solves; default 1e-10 */
     int dsa_max;           /* outer_precond 1: iteration cap of a diffusion solve (its iterate is
                               kept at the cap); default 500 */
+    int cells_3d;          /* 3D cells (Sec. 3.1) built 0 = on the device (one thread per cell),
+                              1 = on the host cores; both give the same cells; default 0 */
 } mlpg_options;
 
 typedef struct {

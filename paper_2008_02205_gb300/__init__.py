@@ -47,7 +47,7 @@ class Options(ctypes.Structure):
                 ("mixed_half_prec", ctypes.c_int), ("outer_method", ctypes.c_int), ("rk_order", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("apply_kernel", ctypes.c_int),
                 ("tile_rows", ctypes.c_int), ("tile_dpt", ctypes.c_int), ("outer_precond", ctypes.c_int),
-                ("dsa_tol", ctypes.c_double), ("dsa_max", ctypes.c_int)]
+                ("dsa_tol", ctypes.c_double), ("dsa_max", ctypes.c_int), ("cells_3d", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -17,7 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(HERE, "libmlpg.so")
 SOURCES = ["api.cu", "neighbors.cu", "assemble.cu", "assemble3d.cu", "cells2d.cu", "operators.cu", "krylov.cu", "noalloc.cu", "geometry.cpp",
-           "quadrature.cpp", "tiles.cpp"]
+           "quadrature.cpp", "tiles.cpp", "cells3d.cu"]
+# per-file flags: the device 3D cell builder rounds like the host builder (no contraction)
+EXTRA = {"cells3d.cu": ["--fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +42,7 @@ def _compile(src):
     if os.path.exists(obj) and all(os.path.getmtime(obj) >= os.path.getmtime(d) for d in deps):
         return obj
     lang = ["-x", "cu"] if src.endswith(".cu") else []
-    cmd = [nvcc()] + _flags() + lang + ["-c", path, "-o", obj]
+    cmd = [nvcc()] + _flags() + EXTRA.get(src, []) + lang + ["-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -100,6 +100,7 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
         (opt->tile_dpt != 0 && opt->tile_dpt != 4 && opt->tile_dpt != 8) ||
         (opt->outer_precond != 0 && opt->outer_precond != 1) || (opt->outer_precond == 1 && opt->outer_method != 0) ||
         (opt->outer_precond == 1 && (!(opt->dsa_tol > 0.0) || opt->dsa_max < 1)) ||
+        (opt->cells_3d != 0 && opt->cells_3d != 1) ||
         (opt->dim == 3 && opt->rk_order != 1) || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
@@ -253,6 +254,7 @@ void mlpg_default_options(mlpg_options *o) {
     o->outer_precond = 0;
     o->dsa_tol = 1e-10;
     o->dsa_max = 500;
+    o->cells_3d = 0;
 }
 
 mlpg_status mlpg_create(const mlpg_options *opt, int64_t n, const double *points, const double *kernel_extent,
@@ -302,7 +304,17 @@ mlpg_status mlpg_integrate(mlpg_ctx *ctx) {
     GUARD(ctx);
     try {
         MLPG_TRY(run_neighbors(ctx));
-        if (ctx->dim == 3) {
+        if (ctx->dim == 3 && ctx->opt.cells_3d == 0) {   // cells on the device
+            MLPG_TRY(run_cells_3d(ctx));
+            MLPG_TRY(run_interp_3d(ctx));
+            MLPG_TRY(build_blocks(ctx));
+            ctx->st.nnz = ctx->nnz;
+            ctx->st.n_volume_qp = ctx->nvq;
+            ctx->st.n_boundary_qp = ctx->nbq;
+            ctx->state = 1;
+            return MLPG_OK;
+        }
+        if (ctx->dim == 3) {   // cells on the host cores
             HostCells3 c3;
             int64_t bad = build_cells_3d(ctx->n, ctx->h_x.data(), ctx->h_R.data(), ctx->opt.lo, ctx->opt.hi,
                                          ctx->h_rowptr.data(), ctx->h_col.data(), c3);
