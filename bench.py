@@ -138,8 +138,11 @@ class ClockSampler:
 
 PROFILE = os.path.join(ROOT, "profiles", "k_spmm32_tile-2d-two-region-256x256-S8.md")
 APPLY_KERNELS = {1: "k_spmm32 (row teams)", 2: "k_spmm32_tile (row tiles, TMA-staged)",
-                 3: "k_spmm32_mma (row tiles, tensor cores)"}
+                 3: "k_spmm32_mma (row tiles, tensor cores)",
+                 4: "k_spmm32_tile (row tiles, gather mode)"}
 KERNEL_SRC = os.path.join(ROOT, "paper_2008_02205_gb300", "csrc", "operators.cu")
+# FP32 FMA peak of the GB300 (TFMA/s): 152 SMs x 128 FP32 lanes x 2.07 GHz maximum SM clock
+FP32_FMA_PEAK_T = 152 * 128 * 2.07e9 / 1e12
 
 
 def _traffic():
@@ -298,9 +301,14 @@ def _apply_3d(pkg, stream):
     us, st = autotune.time_apply(prob, {}, reps=10, warmup=3, stream=stream)
     hbm, kind = _peaks()
     gbs = st["spmm_bytes"] / (us * 1e-6) / 1e9
+    # FP32 FMAs: nine to combine the ten base arrays per entry and direction, one with X
+    fmas = 10.0 * st["nnz"] * prob.m
+    tfma = fmas / (us * 1e-6) / 1e12
     return {"workload": "3d-lognormal-40^3-refined272", "us_per_launch": us, "bytes_per_launch": st["spmm_bytes"],
             "achieved_gbs": gbs, "frac": gbs / hbm, "peak": hbm, "peak_kind": kind,
-            "kernel": "row tiles" if st["apply_kernel"] == 2 else "row teams", "nnz": st["nnz"]}
+            "fma_tfma_s": tfma, "fma_frac": tfma / FP32_FMA_PEAK_T,
+            "kernel": APPLY_KERNELS.get(st["apply_kernel"], "k_spmm32"),
+            "tile_chunk": st["tile_chunk"], "nnz": st["nnz"]}
 
 
 def _serving(pkg, count=10, rates=(2.0, 8.0)):

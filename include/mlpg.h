@@ -79,16 +79,23 @@ typedef struct {
                               neighbours, e.g. extent 2.5-3 point spacings); 3D: 1 only;
                               default 1 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
-    int apply_kernel;      /* MLPG_MIXED batched L-apply: 0 = automatic (row tiles when m % 4 == 0 and
-                              the tile's staged directions fit shared memory), 1 = one team of
+    int apply_kernel;      /* MLPG_MIXED batched L-apply: 0 = automatic (m % 4 == 0: row tiles with a
+                              staged halo when that takes at most two direction chunks, else row
+                              tiles in gather mode; otherwise row teams), 1 = one team of
                               direction lanes per row gathering X through L1, 2 = row tiles with the
                               tile's neighbour rows staged in shared memory (m % 4 == 0), 3 = the
                               same tiles with the combination of the base arrays on tensor cores
-                              (TF32 split in high and low parts: FP32 accuracy; m % 8 == 0);
+                              (TF32 split in high and low parts: FP32 accuracy; m % 8 == 0),
+                              4 = row tiles with only the operator records staged and X read
+                              from global memory (L2) per entry: no halo in shared memory, so a
+                              chunk holds all directions (m % 4 == 0; for large direction sets,
+                              e.g. 3D, whose halos leave room for few directions per chunk);
                               default 0 */
-    int tile_rows;         /* row tiles: rows per tile, 32 or 64; 0 = 64 */
+    int tile_rows;         /* row tiles: rows per tile, 32 or 64 (apply_kernel 2, 3), 4, 8, 16 or
+                              32 (apply_kernel 4); 0 = 64, or in gather mode the most rows that
+                              keep a CTA at or below 320 threads */
     int tile_dpt;          /* row tiles: directions per thread, 4 or 8 (must divide m); 0 = 8 when
-                              m % 8 == 0, else 4 */
+                              m % 8 == 0 with a staged halo, else 4 */
     int outer_precond;     /* outer GMRES on Phi: 0 = none (the paper's), 1 = DSA-like diffusion
                               correction, right preconditioner I + C^-1 Ms with the P1-diffusion
                               operator C = diag(1/(3 sigma_t,i)) sum_a K_aa + kappa M0 + Mt - Ms
@@ -120,7 +127,8 @@ typedef struct {
     int64_t kernel_launches;     /* kernels this context launched since create */
     int64_t device_bytes;        /* device memory this context holds (its own allocations) */
     int32_t apply_kernel;        /* FP32 batched L-apply in use once operators exist: 1 row teams,
-                                    2 row tiles, 3 row tiles on tensor cores (see
+                                    2 row tiles, 3 row tiles on tensor cores, 4 row tiles gathering
+                                    X from global memory (see
                                     mlpg_options.apply_kernel); 0 before */
     int32_t tile_chunk;          /* row tiles: directions per CTA (the chunk), 0 otherwise */
     int64_t tile_max_halo;       /* row tiles: largest halo (staged neighbour rows) of a tile */
@@ -263,8 +271,10 @@ mlpg_status mlpg_get_forms(const mlpg_ctx *ctx, double *mats, double *vecs);
 /* Batched transport operator (Sec. 4.2, operator L): Y[i][m] = (L_m X_m)_i
  * for all directions at once, for the 1/(c dt) of `dt`; X, Y device [n][m]
  * arrays of `precision` (MLPG_FP64: double, MLPG_MIXED: float), queued on the
- * library stream.  MLPG_ERR_STATE before assemble, MLPG_ERR_ARG for another
- * precision or dt <= 0. */
+ * library stream; X and Y must not overlap and must start on 16-byte
+ * boundaries (the kernels move four floats or two doubles at a time).
+ * MLPG_ERR_STATE before assemble, MLPG_ERR_ARG for another precision,
+ * dt <= 0 or a misaligned or overlapping X or Y. */
 mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void *X, void *Y);
 
 /* ---- allocation-free helper ----------------------------------------------- */

@@ -22,7 +22,7 @@ import json
 import os
 import statistics
 
-from . import MLPG_MIXED, TransportProblem, mlpg_apply_L_dev
+from . import MLPG_ERR_ARG, MLPG_MIXED, MlpgError, TransportProblem, mlpg_apply_L_dev
 
 
 def cache_path() -> str:
@@ -42,6 +42,8 @@ def candidates(m: int):
                 continue
             for rows in (64, 32):
                 out.append({"apply_kernel": 2, "tile_rows": rows, "tile_dpt": dpt})
+            for rows in (32, 16, 8, 4):
+                out.append({"apply_kernel": 4, "tile_rows": rows, "tile_dpt": dpt})
     return out
 
 
@@ -72,11 +74,15 @@ def time_apply(prob, options: dict, reps: int = 20, warmup: int = 5, stream=None
     """Median device time (us) of one batched FP32 L-apply of `prob` with
     `options`, and the statistics the library reports for that context."""
     import torch
-    stream = stream or torch.cuda.current_stream()
+    if stream is None or stream.cuda_stream == 0:
+        # the library runs on the stream it is given, or on its own when given the null stream:
+        # time on a stream of ours so that the events bracket its kernels
+        stream = torch.cuda.Stream()
     with TransportProblem.from_problem(prob, precision=MLPG_MIXED, stream=stream.cuda_stream, **options) as tp:
         tp.integrate().assemble()
         X = torch.rand(prob.n, prob.m, device=stream.device, dtype=torch.float32)
         Y = torch.empty_like(X)
+        torch.cuda.synchronize()   # X is written on the current stream, read on `stream`
         for _ in range(warmup):
             mlpg_apply_L_dev(tp.ctx, prob.dt, MLPG_MIXED, X.data_ptr(), Y.data_ptr())
         torch.cuda.synchronize()
@@ -94,11 +100,17 @@ def time_apply(prob, options: dict, reps: int = 20, warmup: int = 5, stream=None
 def tune(prob, reps: int = 20, warmup: int = 5, stream=None, store: bool = True, cands=None):
     """Time every candidate on `prob`; returns (best options, table of
     {config, us, apply_kernel used, chunk, max halo}).  A candidate the
-    library turns down (m not divisible, a tile that does not fit shared
-    memory) is skipped: its context reports the row-team kernel."""
+    library turns down is skipped: a tile shape whose context falls back to
+    the row-team kernel, or one the apply refuses with MLPG_ERR_ARG (no
+    direction chunk fits shared memory)."""
     table = []
     for opt in (cands if cands is not None else candidates(prob.m)):
-        us, st = time_apply(prob, opt, reps, warmup, stream)
+        try:
+            us, st = time_apply(prob, opt, reps, warmup, stream)
+        except MlpgError as e:
+            if e.status != MLPG_ERR_ARG:   # only a shape the library turns down is skipped
+                raise
+            continue
         if opt["apply_kernel"] >= 2 and st["apply_kernel"] != opt["apply_kernel"]:
             continue
         table.append({**opt, "us": us, "tile_chunk": st["tile_chunk"], "tile_max_halo": st["tile_max_halo"]})

@@ -94,9 +94,13 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
         opt->outer_restart > MLPG_MAX_RESTART || opt->mixed_restart < 1 || opt->mixed_restart > MLPG_MAX_RESTART ||
         (opt->mixed_reorth != 0 && opt->mixed_reorth != 1) ||
         (opt->mixed_half_prec != 0 && opt->mixed_half_prec != 1) || opt->rk_order < 0 || opt->rk_order > 2 ||
-        (opt->outer_method != 0 && opt->outer_method != 1) || opt->apply_kernel < 0 || opt->apply_kernel > 3 ||
-        (opt->apply_kernel == 2 && (m & 3) != 0) || (opt->apply_kernel == 3 && (m & 7) != 0) ||
-        (opt->tile_rows != 0 && opt->tile_rows != 32 && opt->tile_rows != 64) ||
+        (opt->outer_method != 0 && opt->outer_method != 1) || opt->apply_kernel < 0 || opt->apply_kernel > 4 ||
+        ((opt->apply_kernel == 2 || opt->apply_kernel == 4) && (m & 3) != 0) ||
+        (opt->apply_kernel == 3 && (m & 7) != 0) ||
+        (opt->tile_rows != 0 && opt->tile_rows != 4 && opt->tile_rows != 8 && opt->tile_rows != 16 &&
+         opt->tile_rows != 32 && opt->tile_rows != 64) ||
+        (opt->tile_rows > 0 && opt->tile_rows < 32 && opt->apply_kernel != 4) ||
+        (opt->tile_rows == 64 && opt->apply_kernel == 4) ||
         (opt->tile_dpt != 0 && opt->tile_dpt != 4 && opt->tile_dpt != 8) ||
         (opt->outer_precond != 0 && opt->outer_precond != 1) || (opt->outer_precond == 1 && opt->outer_method != 0) ||
         (opt->outer_precond == 1 && (!(opt->dsa_tol > 0.0) || opt->dsa_max < 1)) ||
@@ -456,7 +460,7 @@ mlpg_status mlpg_get_stats(const mlpg_ctx *cctx, mlpg_stats *st) {
         ctx->st.spmm_bytes = nnz * (4 + na * 4) + ctx->nb * (4 + nf * 4) + 2 * 4 * (n + 1) + 2 * n * m * 4;
     else
         ctx->st.spmm_bytes = nnz * (4 + 8 * m) + 4 * (n + 1) + 2 * n * m * 8;
-    ctx->st.apply_kernel = ctx->A32 ? (ctx->t_rec ? (ctx->tile_mma ? 3 : 2) : 1) : 0;
+    ctx->st.apply_kernel = ctx->A32 ? (ctx->t_rec ? (ctx->tile_mma ? 3 : (ctx->tile_gather ? 4 : 2)) : 1) : 0;
     ctx->st.tile_chunk = ctx->t_rec ? ctx->tile_chunk : 0;
     ctx->st.tile_max_halo = ctx->t_rec ? ctx->tile_max_halo : 0;
     *st = ctx->st;
@@ -515,6 +519,12 @@ mlpg_status mlpg_get_forms(const mlpg_ctx *cctx, double *mats, double *vecs) {
 mlpg_status mlpg_apply_L_dev(mlpg_ctx *ctx, double dt, int precision, const void *X, void *Y) {
     if (!ctx || !X || !Y || !(dt > 0.0)) return ctx ? set_err(ctx, MLPG_ERR_ARG, "bad apply arguments") : MLPG_ERR_ARG;
     if (ctx->state != 2) return set_err(ctx, MLPG_ERR_STATE, "apply needs an assembled problem");
+    {
+        const uintptr_t x = (uintptr_t)X, y = (uintptr_t)Y;
+        const uintptr_t bytes = (uintptr_t)ctx->n * ctx->m * (precision == MLPG_FP64 ? 8 : 4);
+        if ((x & 15) || (y & 15)) return set_err(ctx, MLPG_ERR_ARG, "X and Y must be 16-byte aligned");
+        if (x < y + bytes && y < x + bytes) return set_err(ctx, MLPG_ERR_ARG, "X and Y overlap");
+    }
     GUARD(ctx);
     try {
         double kappa = std::isfinite(dt) ? 1.0 / (ctx->opt.c * dt) : 0.0;

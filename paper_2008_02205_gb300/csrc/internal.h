@@ -198,6 +198,7 @@ struct mlpg_ctx {
     // row tiles of the FP32 L-apply (tiles.cpp), used when m % 4 == 0
     int tile_rows = 0, tile_chunk = 0, tile_dpt = 0, tile_xs = 0;  // rows per tile, directions per CTA, per thread, smem row stride
     bool tile_mma = false;      // the tensor-core variant of the tiled apply (apply_kernel 3)
+    bool tile_gather = false;   // tiles with X read from global memory, no staged halo (apply_kernel 4)
     int64_t ntile = 0, nslot = 0;
     size_t tile_smem = 0;       // dynamic shared memory of the tiled kernel: halo rows + record stages
     int tile_xs_f4 = 0;         // float4 words of the staged halo (the record stages follow)

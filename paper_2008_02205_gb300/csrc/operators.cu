@@ -481,6 +481,8 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 }
 
 constexpr int kRecK = 4;        // record pipeline: entries (k steps) per stage
+constexpr int kRecKGather = 8;  // ... in gather mode (more entries' loads in flight between barriers)
+__host__ __device__ constexpr int rec_k(bool gather) { return gather ? kRecKGather : kRecK; }
 constexpr int kRecStages = 4;   // record pipeline: stages in flight
 // direction groups per row: threads per CTA = rows per tile x groups (<= 640)
 __host__ __device__ constexpr int tile_max_groups(int tr, int dpt) { return (dpt == 8 ? 320 : 640) / tr; }
@@ -557,7 +559,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // writes Y = L X or Y = B - L X.  Every decision taken on a wait is
 // block-uniform; a wait that gives up sets *err, lets the copies in flight
 // land (bounded waits) and ends the CTA.
-template <int D, int DPT, int TR>
+// GX (gather mode): no halo is staged; a record's index word is the global
+// offset col x m of its column's row, and the thread reads its directions of
+// that row from global memory (L2).  Without the halo in shared memory a
+// chunk holds all directions (up to the thread limit), so the records are
+// streamed once per tile, not once per chunk: the choice for large direction
+// sets, whose halos leave room for only a few directions per chunk.
+template <int D, int DPT, int TR, bool GX>
 __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     int m, int mc, int xs, int hx_f4, const int32_t *__restrict__ base, const int32_t *__restrict__ width,
     const int32_t *__restrict__ trow, const int32_t *__restrict__ hptr, const int32_t *__restrict__ hcol,
@@ -565,7 +573,8 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     const int32_t *__restrict__ bhalo, const float *__restrict__ bval, int64_t nb, const float *__restrict__ X,
     const float *__restrict__ B, float *__restrict__ Y, int *__restrict__ err) {
     constexpr int K = NA<D>(), RW4 = rec_words<D>() / 4, NQ = DPT / 4, NS = kRecStages;
-    constexpr int SF4 = kRecK * TR * RW4;   // float4 per record stage
+    constexpr int RK = rec_k(GX);            // entries per record stage
+    constexpr int SF4 = RK * TR * RW4;      // float4 per record stage
     constexpr uint32_t SBYTES = SF4 * 16u;
     extern __shared__ float4 smem_x4[];
     __shared__ __align__(8) uint64_t bars[NS + 1];   // record stages, then the halo
@@ -573,7 +582,7 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     float4 *Rs = smem_x4 + hx_f4;
     const int t = blockIdx.x, m0 = blockIdx.y * mc, mcw = min(mc, m - m0), G = mc / DPT;
     const int s = threadIdx.x / G, g = threadIdx.x - s * G;
-    const int W = width[t], nst = W / kRecK;
+    const int W = width[t], nst = W / RK;
     const float4 *rg = rec + (int64_t)base[t] * RW4;
     const int h0 = hptr[t], hn = hptr[t + 1] - h0;
     const uint32_t row_bytes = (uint32_t)mcw * 4u;
@@ -583,14 +592,17 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect(&bars[NS], (uint32_t)hn * row_bytes);
+        if constexpr (!GX) mbar_expect(&bars[NS], (uint32_t)hn * row_bytes);
         for (int st = 0; st < NS && st < nst; ++st) {
             mbar_expect(&bars[st], SBYTES);
             bulk_g2s(Rs + st * SF4, rg + (int64_t)st * SF4, SBYTES, &bars[st]);
         }
     }
-    for (int hh = threadIdx.x; hh < hn; hh += blockDim.x)
-        bulk_g2s(Xs + hh * xs, X + (int64_t)hcol[h0 + hh] * m + m0, row_bytes, &bars[NS]);
+    if constexpr (!GX)
+        for (int hh = threadIdx.x; hh < hn; hh += blockDim.x)
+            bulk_g2s(Xs + hh * xs, X + (int64_t)hcol[h0 + hh] * m + m0, row_bytes, &bars[NS]);
+    // GX: X is read from global memory, at the chunk's first direction
+    const float *Xg = X + m0;
     // the thread's directions and their coefficient pairs
     int qoff[NQ];
     bool on[NQ];
@@ -611,27 +623,31 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     float2 acc[2 * NQ];
 #pragma unroll
     for (int j = 0; j < 2 * NQ; ++j) acc[j] = make_float2(0.0f, 0.0f);
-    bool ok = __syncthreads_and(mbar_wait(&bars[NS], 0));
+    bool ok = true;
+    if constexpr (!GX) ok = __syncthreads_and(mbar_wait(&bars[NS], 0));
     int st = 0;
     for (; st < nst && ok; ++st) {
         const int b = st % NS;
         if (!__syncthreads_and(mbar_wait(&bars[b], (st / NS) & 1))) { ok = false; break; }
         const float4 *rb = Rs + b * SF4 + s * RW4;
 #pragma unroll
-        for (int kk = 0; kk < kRecK; ++kk) {
+        for (int kk = 0; kk < RK; ++kk) {
             float a[4 * RW4];
 #pragma unroll
             for (int q = 0; q < RW4; ++q) {
                 const float4 v = rb[kk * TR * RW4 + q];
                 a[4 * q] = v.x; a[4 * q + 1] = v.y; a[4 * q + 2] = v.z; a[4 * q + 3] = v.w;
             }
-            const float *xr = Xs + __float_as_int(a[K]);
+            const float *xr = (GX ? Xg : Xs) + __float_as_int(a[K]);
             float2 ab[K];   // the entry's values, each in both halves of a pair
 #pragma unroll
             for (int k2 = 0; k2 < K; ++k2) ab[k2] = make_float2(a[k2], a[k2]);
 #pragma unroll
             for (int u = 0; u < NQ; ++u) {
-                const float4 x4 = *reinterpret_cast<const float4 *>(xr + qoff[u]);
+                // GX: a quad past the last chunk's directions is not read (it may lie past X)
+                const float4 x4 = !GX ? *reinterpret_cast<const float4 *>(xr + qoff[u])
+                                      : (on[u] ? __ldg(reinterpret_cast<const float4 *>(xr + qoff[u]))
+                                               : make_float4(0.0f, 0.0f, 0.0f, 0.0f));
                 const float2 xp[2] = {make_float2(x4.x, x4.y), make_float2(x4.z, x4.w)};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -651,7 +667,7 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
     if (!ok) {   // (block-uniform) report, let the copies in flight land, leave
         if (threadIdx.x == 0) {
             atomicOr(err, 1);
-            mbar_wait(&bars[NS], 0);
+            if constexpr (!GX) mbar_wait(&bars[NS], 0);
             for (int k = st; k < nst && k < st + NS; ++k) mbar_wait(&bars[k % NS], (k / NS) & 1);
         }
         __syncthreads();
@@ -674,7 +690,7 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
                                                    coef32[16 * (d0 + 1) + face_slot<D>() + f]);
             }
         for (int32_t q = q0; q < q1; ++q) {
-            const float *xr = Xs + bhalo[q];
+            const float *xr = (GX ? Xg : Xs) + bhalo[q];
             float2 sv[NF<D>()];
 #pragma unroll
             for (int f = 0; f < NF<D>(); ++f) {
@@ -683,7 +699,8 @@ __global__ void __launch_bounds__(TR * tile_max_groups(TR, DPT)) k_spmm32_tile(
             }
 #pragma unroll
             for (int u = 0; u < NQ; ++u) {
-                const float4 x4 = *reinterpret_cast<const float4 *>(xr + qoff[u]);
+                const float4 x4 = (GX && !on[u]) ? make_float4(0.0f, 0.0f, 0.0f, 0.0f)
+                                                 : *reinterpret_cast<const float4 *>(xr + qoff[u]);
                 const float2 xp[2] = {make_float2(x4.x, x4.y), make_float2(x4.z, x4.w)};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -1442,18 +1459,21 @@ static int64_t team_grid(int64_t n, const Team &) { return (n * 32 + 255) / 256;
 static int64_t rowteam_grid(int64_t n, const Team &tm) { return ((n << tm.tm_log2) + 255) / 256; }
 
 // Row tiles of the FP32 L-apply: built once per point set when m % 4 == 0.
-// Tile shape: TR rows per tile (32 or 64) and DPT directions per thread (8
-// when m % 8 == 0, else 4), from the options or, by default, 64 rows and the
-// larger DPT; G = chunk / DPT thread groups per row.  The directions are split
-// into chunks (one CTA each) until a tile's staged halo, halo x (chunk + 4)
-// floats, and the record stages fit kTileSmem.
+// Tile shape: TR rows per tile and DPT directions per thread, from the options
+// or by default 64 rows and 8 directions (4 when m % 8 != 0) with a staged
+// halo, 4 directions and at most 320 threads per CTA in gather mode; G = chunk
+// / DPT thread groups per row.  The directions are split into chunks (one CTA
+// each) until a tile's staged halo, halo x (chunk + 4) floats, and the record
+// stages fit kTileSmem (staged halo), or until G fits the thread limit
+// (gather).  The automatic choice stages the halo while that takes at most
+// two chunks, and gathers otherwise.
 constexpr size_t kTileSmem = 100 * 1024;
 
-template <int D, int DPT, int TR>
+template <int D, int DPT, int TR, bool GX>
 static mlpg_status launch_tile(mlpg_ctx *ctx, const float *X, const float *B, float *Y) {
     const dim3 tg((unsigned)ctx->ntile, (unsigned)((ctx->m + ctx->tile_chunk - 1) / ctx->tile_chunk));
     const int threads = TR * (ctx->tile_chunk / DPT);
-    k_spmm32_tile<D, DPT, TR><<<tg, threads, ctx->tile_smem, ctx->stream>>>(
+    k_spmm32_tile<D, DPT, TR, GX><<<tg, threads, ctx->tile_smem, ctx->stream>>>(
         ctx->m, ctx->tile_chunk, ctx->tile_xs, ctx->tile_xs_f4, ctx->t_base, ctx->t_width, ctx->t_row, ctx->t_hptr,
         ctx->t_hcol, reinterpret_cast<const float4 *>(ctx->t_rec), ctx->coef32, ctx->bptr, ctx->t_bhalo, ctx->bval32,
         ctx->nb, X, B, Y, ctx->d_tile_err);
@@ -1492,63 +1512,129 @@ static mlpg_status run_tile(mlpg_ctx *ctx, const float *X, const float *B, float
         MMA_NT_SWITCH(D, 64, launch_mma, ctx, X, B, Y)
     }
     const int key = ctx->tile_dpt * 100 + ctx->tile_rows;
+    if (ctx->tile_gather) switch (key) {
+            case 804: return launch_tile<D, 8, 4, true>(ctx, X, B, Y);
+            case 404: return launch_tile<D, 4, 4, true>(ctx, X, B, Y);
+            case 808: return launch_tile<D, 8, 8, true>(ctx, X, B, Y);
+            case 816: return launch_tile<D, 8, 16, true>(ctx, X, B, Y);
+            case 832: return launch_tile<D, 8, 32, true>(ctx, X, B, Y);
+            case 408: return launch_tile<D, 4, 8, true>(ctx, X, B, Y);
+            case 416: return launch_tile<D, 4, 16, true>(ctx, X, B, Y);
+            default: return launch_tile<D, 4, 32, true>(ctx, X, B, Y);
+        }
     switch (key) {
-        case 832: return launch_tile<D, 8, 32>(ctx, X, B, Y);
-        case 864: return launch_tile<D, 8, 64>(ctx, X, B, Y);
-        case 432: return launch_tile<D, 4, 32>(ctx, X, B, Y);
-        default: return launch_tile<D, 4, 64>(ctx, X, B, Y);
+        case 832: return launch_tile<D, 8, 32, false>(ctx, X, B, Y);
+        case 864: return launch_tile<D, 8, 64, false>(ctx, X, B, Y);
+        case 432: return launch_tile<D, 4, 32, false>(ctx, X, B, Y);
+        default: return launch_tile<D, 4, 64, false>(ctx, X, B, Y);
     }
 }
-template <int D, int DPT, int TR>
+template <int D, int DPT, int TR, bool GX>
 static mlpg_status tile_attr(mlpg_ctx *ctx) {
     // the kernel's attribute is shared by every context: set to the fixed budget, never lowered
-    CU(ctx, cudaFuncSetAttribute(k_spmm32_tile<D, DPT, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // (the record stages of 32-row gather tiles alone reach the 48 KB default)
+    CU(ctx, cudaFuncSetAttribute(k_spmm32_tile<D, DPT, TR, GX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kTileSmem));
     return MLPG_OK;
 }
 
-template <int D>
-static mlpg_status init_tiles(mlpg_ctx *ctx) {
-    const int m = ctx->m;
-    if ((m & 3) != 0 || ctx->opt.apply_kernel == 1) return MLPG_OK;
-    const int tr = ctx->opt.tile_rows ? ctx->opt.tile_rows : 64;
-    const int dpt = ctx->opt.tile_dpt ? ctx->opt.tile_dpt : ((m & 7) == 0 ? 8 : 4);
-    if (m % dpt != 0) return set_err(ctx, MLPG_ERR_ARG, "tile_dpt must divide the number of directions");
+// One tile layout: rows per tile, directions per thread and per CTA (chunk),
+// staged halo or gather mode, the host-side tiles.  chunk == 0: no layout.
+struct TilePlan {
+    int tr = 0, dpt = 0, chunk = 0;
+    bool gather = false, mma = false;
+    size_t rec_smem = 0;
     TileLayout tl;
-    const int64_t nslot = build_tiles(ctx->n, ctx->h_rowptr.data(), ctx->h_col.data(), ctx->h_order.data(), tr,
-                                      kRecK, tl);
-    if (nslot * (int64_t)(rec_words<D>() / 4) >= (int64_t(1) << 31) || tl.hptr.back() >= (int64_t(1) << 31))
+    int64_t nslot = 0;
+};
+
+// Plans the tiles of one mode; an explicit request that cannot be met is an
+// error, the automatic choice only finds no layout (chunk 0).
+template <int D>
+static mlpg_status plan_tiles(mlpg_ctx *ctx, bool gather, bool mma, TilePlan &P) {
+    const int m = ctx->m;
+    const bool ask = ctx->opt.apply_kernel != 0;
+    P = TilePlan();
+    P.gather = gather;
+    P.mma = mma;
+    // gather: four directions per thread measured fastest (more CTAs per SM)
+    const int dpt = ctx->opt.tile_dpt ? ctx->opt.tile_dpt : ((m & 7) == 0 && !gather ? 8 : 4);
+    if (m % dpt != 0) return set_err(ctx, MLPG_ERR_ARG, "tile_dpt must divide the number of directions");
+    int tr = ctx->opt.tile_rows;
+    if (gather && tr == 0) {   // the most rows per tile with at most 320 threads per CTA
+        const int G = (m + dpt - 1) / dpt;
+        tr = 4;
+        for (int c : {32, 16, 8})
+            if (c * G <= 320) {
+                tr = c;
+                break;
+            }
+    }
+    if (tr == 0) tr = 64;
+    if (gather && tr == 64)
+        return ask ? set_err(ctx, MLPG_ERR_ARG, "apply_kernel 4 takes 4, 8, 16 or 32 rows per tile") : MLPG_OK;
+    if (gather && (int64_t)ctx->n * m >= (int64_t(1) << 31))
+        return ask ? set_err(ctx, MLPG_ERR_ARG, "apply_kernel 4 needs n x m < 2^31 (32-bit record offsets)") : MLPG_OK;
+    const int rk = rec_k(gather);
+    P.nslot = build_tiles(ctx->n, ctx->h_rowptr.data(), ctx->h_col.data(), ctx->h_order.data(), tr, rk, P.tl);
+    const TileLayout &tl = P.tl;
+    if (P.nslot * (int64_t)(rec_words<D>() / 4) >= (int64_t(1) << 31) || tl.hptr.back() >= (int64_t(1) << 31))
         return MLPG_OK;   // beyond 32-bit slot indices: the row-team kernel serves
-    const size_t rec_smem = (size_t)kRecStages * kRecK * tr * (rec_words<D>() / 4) * sizeof(float4);
+    P.rec_smem = (size_t)kRecStages * rk * tr * (rec_words<D>() / 4) * sizeof(float4);
     int chunk = 0;
-    const bool mma = ctx->opt.apply_kernel == 3;
     if (mma) {
         // tensor-core tiles: chunks of 8 NT directions (NT <= 6) dividing m; shared-memory row stride
         // 16 mod 32 words (two rows read by one 8-lane phase then fall on disjoint banks half the time)
         if ((m & 7) != 0) return set_err(ctx, MLPG_ERR_ARG, "apply_kernel 3 needs a multiple of 8 directions");
         for (int nt = 6; nt >= 2 && !chunk; --nt) {
             const int mc = 8 * nt, xs = mc + (16 - mc % 32 + 32) % 32;
-            if (m % mc == 0 && (size_t)tl.max_halo * xs * sizeof(float) + rec_smem <= kTileSmem) chunk = mc;
+            if (m % mc == 0 && (size_t)tl.max_halo * xs * sizeof(float) + P.rec_smem <= kTileSmem) chunk = mc;
         }
         if (!chunk) return set_err(ctx, MLPG_ERR_ARG, "apply_kernel 3: no direction chunk fits shared memory");
     }
     for (int nchunk = 1; nchunk <= m / 4 && !mma; ++nchunk) {
         const int G = (m + dpt * nchunk - 1) / (dpt * nchunk);
         if (G > tile_max_groups(tr, dpt)) continue;
-        if ((size_t)tl.max_halo * (G * dpt + 4) * sizeof(float) + rec_smem <= kTileSmem) {
+        if (gather || (size_t)tl.max_halo * (G * dpt + 4) * sizeof(float) + P.rec_smem <= kTileSmem) {
             chunk = G * dpt;
             break;
         }
     }
-    // automatic choice: staging pays only while the operator records are read
-    // by few chunks; the row-team kernel otherwise
-    if (chunk == 0 || (ctx->opt.apply_kernel == 0 && (m + chunk - 1) / chunk > 2)) return MLPG_OK;
+    P.tr = tr;
+    P.dpt = dpt;
+    P.chunk = chunk;
+    return MLPG_OK;
+}
+
+template <int D>
+static mlpg_status init_tiles(mlpg_ctx *ctx) {
+    const int m = ctx->m, kind = ctx->opt.apply_kernel;
+    if ((m & 3) != 0 || kind == 1) return MLPG_OK;
+    TilePlan P;
+    if (kind != 4) {
+        MLPG_TRY(plan_tiles<D>(ctx, false, kind == 3, P));
+        // automatic choice: staged halos pay while the records are read by few chunks;
+        // past two chunks the gather mode reads them once
+        if (kind == 0 && P.chunk && (m + P.chunk - 1) / P.chunk > 2) P.chunk = 0;
+    }
+    if (kind == 4 || (kind == 0 && P.chunk == 0)) MLPG_TRY(plan_tiles<D>(ctx, true, false, P));
+    if (P.chunk == 0) return MLPG_OK;
+    const int tr = P.tr, dpt = P.dpt, chunk = P.chunk;
+    const bool gather = P.gather, mma = P.mma;
+    const size_t rec_smem = P.rec_smem;
+    const int64_t nslot = P.nslot;
+    TileLayout &tl = P.tl;
     ctx->tile_rows = tr;
     ctx->tile_dpt = dpt;
     ctx->tile_chunk = chunk;
     ctx->tile_mma = mma;
-    ctx->tile_xs = mma ? chunk + (16 - chunk % 32 + 32) % 32
-                       : chunk + 4;   // padded shared-memory row: spreads halo rows over the banks
+    ctx->tile_gather = gather;
+    // gather: the record index is the column's global offset col x m; otherwise the column's
+    // staged row in shared memory, a padded row that spreads halo rows over the banks
+    ctx->tile_xs = gather ? m : (mma ? chunk + (16 - chunk % 32 + 32) % 32 : chunk + 4);
+    if (gather) {   // global columns of the slots (zero for padding: a zero record)
+        for (int64_t e = 0; e < nslot; ++e) tl.lcol[e] = tl.perm[e] >= 0 ? ctx->h_col[tl.perm[e]] : 0;
+    }
     ctx->ntile = tl.ntile;
     ctx->nslot = nslot;
     cudaStream_t s = ctx->stream;
@@ -1581,6 +1667,10 @@ static mlpg_status init_tiles(mlpg_ctx *ctx) {
         for (int64_t r = 0; r < tl.ntile * tr; ++r) {
             const int32_t i = tl.row[r];
             if (i < 0) continue;
+            if (gather) {
+                for (int32_t q = bptr[i]; q < bptr[i + 1]; ++q) bhalo[q] = bcol[q] * m;
+                continue;
+            }
             const int64_t t = r / tr;
             const int32_t *hb = tl.hcol.data() + tl.hptr[t], *he = tl.hcol.data() + tl.hptr[t + 1];
             for (int32_t q = bptr[i]; q < bptr[i + 1]; ++q) {
@@ -1602,13 +1692,23 @@ static mlpg_status init_tiles(mlpg_ctx *ctx) {
         };
         st = set();
         if (st != MLPG_OK) return st;
-    } else switch (dpt * 100 + tr) {
-        case 832: MLPG_TRY((tile_attr<D, 8, 32>(ctx))); break;
-        case 864: MLPG_TRY((tile_attr<D, 8, 64>(ctx))); break;
-        case 432: MLPG_TRY((tile_attr<D, 4, 32>(ctx))); break;
-        default: MLPG_TRY((tile_attr<D, 4, 64>(ctx))); break;
-    }
-    ctx->tile_xs_f4 = (int)(tl.max_halo * ctx->tile_xs / 4);
+    } else if (gather) switch (dpt * 100 + tr) {
+            case 804: MLPG_TRY((tile_attr<D, 8, 4, true>(ctx))); break;
+            case 808: MLPG_TRY((tile_attr<D, 8, 8, true>(ctx))); break;
+            case 816: MLPG_TRY((tile_attr<D, 8, 16, true>(ctx))); break;
+            case 832: MLPG_TRY((tile_attr<D, 8, 32, true>(ctx))); break;
+            case 404: MLPG_TRY((tile_attr<D, 4, 4, true>(ctx))); break;
+            case 408: MLPG_TRY((tile_attr<D, 4, 8, true>(ctx))); break;
+            case 416: MLPG_TRY((tile_attr<D, 4, 16, true>(ctx))); break;
+            default: MLPG_TRY((tile_attr<D, 4, 32, true>(ctx))); break;
+        }
+    else switch (dpt * 100 + tr) {
+            case 832: MLPG_TRY((tile_attr<D, 8, 32, false>(ctx))); break;
+            case 864: MLPG_TRY((tile_attr<D, 8, 64, false>(ctx))); break;
+            case 432: MLPG_TRY((tile_attr<D, 4, 32, false>(ctx))); break;
+            default: MLPG_TRY((tile_attr<D, 4, 64, false>(ctx))); break;
+        }
+    ctx->tile_xs_f4 = gather ? 0 : (int)(tl.max_halo * ctx->tile_xs / 4);
     ctx->tile_smem = (size_t)ctx->tile_xs_f4 * sizeof(float4) + rec_smem;
     ctx->tile_max_halo = tl.max_halo;
     if (!ctx->d_tile_err) {

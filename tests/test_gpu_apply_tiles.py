@@ -25,8 +25,8 @@ def _rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def _apply(prob, X, kernel, dt):
-    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, apply_kernel=kernel) as tp:
+def _apply(prob, X, kernel, dt, **opts):
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, apply_kernel=kernel, **opts) as tp:
         tp.integrate().assemble()
         Xd = torch.tensor(X, dtype=torch.float32, device="cuda")
         Yd = torch.full_like(Xd, float("nan"))
@@ -138,3 +138,79 @@ def test_mixed_run_through_tiles_matches_oracle():
         assert tp.stats()["apply_kernel"] == 2
     ref = O.solve_problem(prob)
     assert _rel(phi, ref) < 1e-8
+
+
+GATHER_CASES = [
+    # (dim, points per side, S_N or refined set, rows per tile, directions per thread, expected chunk)
+    (2, 13, 4, 8, 4, 12),      # m = 12, 169 points: 22 tiles of 8 rows, the last ragged
+    (2, 30, 8, 32, 8, 40),     # the benchmark's angular set
+    (2, 17, 12, 32, 4, 44),    # m = 84: two chunks of 44 and 40 (the last chunk's spare lanes read nothing)
+    (3, 6, 4, 16, 8, 24),      # 3D, m = 24
+    (3, 7, 8, 8, 8, 80),       # 3D, m = 80 in one chunk (the staged-halo tiles need several)
+    (3, 7, 8, 4, 4, 80),       # 3D, 4-row tiles
+    (3, 5, "refined", 0, 0, None),  # 3D, Alg. 2 set, automatic tile shape
+]
+
+
+@pytest.mark.parametrize("dim,side,sn,rows,dpt,chunk", GATHER_CASES)
+def test_gather_tiles_match_oracle_and_row_teams(dim, side, sn, rows, dpt, chunk):
+    """apply_kernel 4: the tile's records staged in shared memory, X read from
+    global memory; the same arithmetic as the staged-halo tiles."""
+    if dim == 2:
+        prob = mi.two_region_2d(n_per_dim=side, sn=sn, seed=2100 + side)
+    elif sn == "refined":
+        prob = mi.lognormal_3d(side, seed=3100 + side, refine=(0, 2, 30.0))
+    else:
+        prob = mi.lognormal_3d(side, sn=sn, seed=3100 + side)
+    rng = np.random.default_rng(17)
+    X = rng.uniform(-1.0, 1.0, (prob.n, prob.m))
+    Yt, st = _apply(prob, X, 4, prob.dt, tile_rows=rows, tile_dpt=dpt)
+    assert st["apply_kernel"] == 4
+    if chunk is not None:
+        assert st["tile_chunk"] == chunk
+    Yr, _ = _apply(prob, X, 1, prob.dt)
+    disc = O.Discretization(prob.x, prob.R, prob.lo, prob.hi)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    tr = O.Transport(disc, F, prob.omega, prob.w)
+    ref = np.stack([tr.L_matrix(m, 1.0 / prob.dt) @ X[:, m] for m in range(prob.m)], axis=1)
+    assert np.all(np.isfinite(Yt))
+    assert _rel(Yt, ref) < 3e-6
+    assert _rel(Yt, Yr) < 3e-6
+
+
+def test_gather_tiles_at_the_3d_configuration_size():
+    """40^3 points, 272 directions (the refined 3D set): the automatic choice
+    is gather mode with all directions in one chunk of 4-row tiles; against
+    the row-team kernel on the same operators (both FP32, parity-tested
+    against the oracle above)."""
+    prob = mi.lognormal_3d(refine=(1, 5, 15.0))
+    X = np.random.default_rng(19).uniform(-1.0, 1.0, (prob.n, prob.m))
+    Yt, st = _apply(prob, X, 0, prob.dt)   # the automatic choice at this size
+    assert st["apply_kernel"] == 4 and st["tile_chunk"] == 272
+    Yr, _ = _apply(prob, X, 1, prob.dt)
+    assert np.all(np.isfinite(Yt))
+    assert _rel(Yt, Yr) < 3e-6
+
+
+def test_mixed_run_through_gather_tiles_matches_oracle():
+    prob = mi.two_region_2d(n_per_dim=18, sn=8, seed=2218, steps=3)
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED, apply_kernel=4) as tp:
+        tp.integrate().assemble()
+        phi = tp.run(prob.dt, prob.steps)
+        assert tp.stats()["apply_kernel"] == 4
+    ref = O.solve_problem(prob)
+    assert _rel(phi, ref) < 1e-8
+
+
+def test_apply_rejects_misaligned_and_overlapping_vectors():
+    prob = mi.two_region_2d(n_per_dim=10, sn=4, seed=2210)
+    with pkg.TransportProblem.from_problem(prob, precision=pkg.MLPG_MIXED) as tp:
+        tp.integrate().assemble()
+        buf = torch.zeros(3 * prob.n * prob.m + 8, dtype=torch.float32, device="cuda")
+        x = buf.data_ptr()
+        y = x + 4 * (prob.n * prob.m + 4)
+        for bad_x, bad_y in ((x + 4, y), (x, y + 8), (x, x + 16)):
+            with pytest.raises(pkg.MlpgError):
+                pkg.mlpg_apply_L_dev(tp.ctx, prob.dt, pkg.MLPG_MIXED, bad_x, bad_y)
+        pkg.mlpg_apply_L_dev(tp.ctx, prob.dt, pkg.MLPG_MIXED, x, y)
+        torch.cuda.synchronize()
