@@ -278,6 +278,7 @@ static void launch_cgs(dim3 grid, cudaStream_t s, int64_t n, int M, int MB, int 
 //                 in shared memory)
 // Block sums go to partial[(l * M + m) * G + block], G = gridDim.x.
 constexpr int kDotGroup = 8;
+constexpr int kGsBlocksPerSm = 4;   // grid of the vectorised passes (measured: 2 -> 4 saves 2.7 % of a step, 8 loses)
 constexpr int kDsaRestart = 30;   // restart length of the diffusion solves
 constexpr size_t kUpdSmem = 96 * 1024;   // largest staged Hessenberg column block of k_cgsv_upd
 template <typename T> struct Vec16;
@@ -431,18 +432,29 @@ __global__ void k_givens(int M, int R, int j, int G, const double *__restrict__ 
         return;
     }
     const double nrm2 = warp_sum_partials(partial + (int64_t)m * G, G, lane);
-    if (lane != 0) return;
-    double hn = sqrt(nrm2);
+    const double hn = sqrt(nrm2);
     double *Hm = H + (int64_t)m * (R + 1) * R;  // Hm[row * R + col]
-    for (int l = 0; l <= j; ++l) Hm[l * R + j] = h1[l * M + m] + (h2 ? h2[l * M + m] : 0.0);
-    Hm[(j + 1) * R + j] = hn;
-    for (int l = 0; l < j; ++l) {
-        double c = cs[m * R + l], sv = sn[m * R + l];
-        double a = Hm[l * R + j], b = Hm[(l + 1) * R + j];
-        Hm[l * R + j] = c * a + sv * b;
-        Hm[(l + 1) * R + j] = -sv * a + c * b;
+    // lane l holds entry l of the new column (l <= j < R <= 32) and the earlier rotation l (l < j);
+    // every lane runs the same rotation chain down the column in registers and keeps its own entry
+    double hl = 0.0, cl = 1.0, sl = 0.0;
+    if (lane <= j) hl = h1[lane * M + m] + (h2 ? h2[lane * M + m] : 0.0);
+    if (lane < j) {
+        cl = cs[m * R + lane];
+        sl = sn[m * R + lane];
     }
-    double a = Hm[j * R + j], b = Hm[(j + 1) * R + j];
+    double carry = __shfl_sync(0xffffffffu, hl, 0), mine = 0.0;
+    for (int l = 0; l < j; ++l) {
+        const double c = __shfl_sync(0xffffffffu, cl, l), sv = __shfl_sync(0xffffffffu, sl, l);
+        const double b = __shfl_sync(0xffffffffu, hl, l + 1);
+        const double a = carry;
+        const double r = c * a + sv * b;
+        carry = -sv * a + c * b;
+        if (lane == l) mine = r;
+    }
+    if (lane < j) Hm[lane * R + j] = mine;
+    if (lane != 0) return;
+    // the new rotation zeroes the subdiagonal entry hn
+    double a = carry, b = hn;
     double den = hypot(a, b);
     double c = den > 0.0 ? a / den : 1.0, sv = den > 0.0 ? b / den : 0.0;
     cs[m * R + j] = c;
@@ -764,16 +776,17 @@ static mlpg_status gmres_solve(mlpg_ctx *ctx, Gmres<T> &G, const ApplyFn<T> &A, 
                 // single classical pass, 16-byte vectors: dots (groups of kDotGroup
                 // basis vectors per grid row), reduce, update + norm partials
                 const int ng = (nl + kDotGroup - 1) / kDotGroup;
-                // two blocks per SM: enough loads in flight, few partial sums for k_reduce / k_givens
-                const int gd = (int)std::max<int64_t>(1, std::min<int64_t>(vrows, (2 * sm_count() + ng - 1) / ng));
-                if ((int64_t)gd * nl * M > G.partial_cap || (int64_t)2 * sm_count() * M > G.partial_cap)
+                // kGsBlocksPerSm blocks per SM: enough loads in flight, few partial sums for k_reduce / k_givens
+                const int gd = (int)std::max<int64_t>(
+                    1, std::min<int64_t>(vrows, (kGsBlocksPerSm * sm_count() + ng - 1) / ng));
+                if ((int64_t)gd * nl * M > G.partial_cap || (int64_t)kGsBlocksPerSm * sm_count() * M > G.partial_cap)
                     return set_err(ctx, MLPG_ERR_ARG, "reduction buffer too small");
                 k_cgsv_dots<T><<<dim3(gd, ng), kBlock, 0, s>>>(n, M, nl, G.V, vs, w, G.partial);
                 CU_LAUNCH(ctx);
                 k_reduce<<<(int)(((int64_t)nl * M * 32 + kBlock - 1) / kBlock), kBlock, 0, s>>>(M, nl, gd, G.partial,
                                                                                               G.h);
                 CU_LAUNCH(ctx);
-                const int gu = (int)std::max<int64_t>(1, std::min<int64_t>(vrows, 2 * sm_count()));
+                const int gu = (int)std::max<int64_t>(1, std::min<int64_t>(vrows, kGsBlocksPerSm * sm_count()));
                 k_cgsv_upd<T><<<gu, kBlock, (size_t)nl * M * sizeof(Ar), s>>>(n, M, nl, G.V, vs, G.h, w, G.partial);
                 CU_LAUNCH(ctx);
                 gnorm = gu;
