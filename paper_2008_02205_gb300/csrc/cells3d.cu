@@ -92,11 +92,13 @@ __device__ int plane_hull(P3 *pts, int np, const P3 &nh, double dist_tol, double
     return m - 1;
 }
 
-// keep {p : nrm . p <= c}; the new face gets label j.  False on overflow.
-__device__ bool clip3(Poly &F, Poly &T, P3 *onp, P3 *hull, Q2 *q, Q2 *h, const P3 &nrm, double c, double eps,
-                      double dist_tol, double area_tol, int32_t j) {
+// keep {p : nrm . p <= c}; the new face gets label j.  *cut: the result is in
+// T (F is unchanged otherwise).  False on overflow.
+__device__ bool clip3(const Poly &F, Poly &T, bool *cut, P3 *onp, P3 *hull, Q2 *q, Q2 *h, const P3 &nrm, double c,
+                      double eps, double dist_tol, double area_tol, int32_t j) {
     bool any_out = false;
     for (int k = 0; k < F.nvt && !any_out; ++k) any_out = dotp(nrm, F.v[k]) - c > eps;
+    *cut = any_out;
     if (!any_out) return true;
     T.nf = 0;
     T.nvt = 0;
@@ -143,16 +145,17 @@ __device__ bool clip3(Poly &F, Poly &T, P3 *onp, P3 *hull, Q2 *q, Q2 *h, const P
         ++T.nf;
         for (int k = 0; k < nh; ++k) T.v[T.nvt++] = hull[k];
     }
-    // F <- T
-    F.nf = T.nf;
-    F.nvt = T.nvt;
-    for (int f = 0; f < T.nf; ++f) {
-        F.f0[f] = T.f0[f];
-        F.nv[f] = T.nv[f];
-        F.lab[f] = T.lab[f];
-    }
-    for (int k = 0; k < T.nvt; ++k) F.v[k] = T.v[k];
     return true;
+}
+
+// largest squared distance of a vertex from g
+__device__ double reach2(const Poly &F, const P3 &g) {
+    double r2 = 0.0;
+    for (int k = 0; k < F.nvt; ++k) {
+        const P3 e = sub(F.v[k], g);
+        r2 = fmax(r2, dotp(e, e));
+    }
+    return r2;
 }
 
 struct Cell3Args {
@@ -174,8 +177,10 @@ __global__ void __launch_bounds__(64) k_cells_3d(Cell3Args A, Poly *work, P3 *on
     const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (li >= A.n) return;
     const int64_t i = A.i0 + li;
-    // per-thread work buffers in global memory (one slot per thread of the slab)
-    Poly &F = work[2 * li], &T = work[2 * li + 1];
+    // per-thread work buffers in global memory (one slot per thread of the slab): the
+    // current polyhedron and the next, swapped after every cut
+    Poly *pf = work + 2 * li, *pt = pf + 1;
+    Poly &F0 = *pf;   // the starting polyhedron
     P3 *onp = onbuf + 2 * kMaxOn * li, *hull = onp + kMaxOn;
     Q2 *q = qbuf + 3 * kMaxOn * li, *h = q + kMaxOn;   // h: room for the two chains, 2 kMaxOn
     const P3 g{A.x[3 * i], A.x[3 * i + 1], A.x[3 * i + 2]};
@@ -190,29 +195,55 @@ __global__ void __launch_bounds__(64) k_cells_3d(Cell3Args A, Poly *work, P3 *on
     }
     // the six faces of the box, counter-clockwise about their outward normals
     const int quad[6][4] = {{0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6}};
-    F.nf = 6;
-    F.nvt = 24;
+    F0.nf = 6;
+    F0.nvt = 24;
     for (int f = 0; f < 6; ++f) {
         const bool dom = (f & 1) ? dhi[f / 2] : dlo[f / 2];
-        F.f0[f] = 4 * f;
-        F.nv[f] = 4;
-        F.lab[f] = dom ? -(f + 1) : kLabelExtent;
+        F0.f0[f] = 4 * f;
+        F0.nv[f] = 4;
+        F0.lab[f] = dom ? -(f + 1) : kLabelExtent;
         for (int k = 0; k < 4; ++k) {
             const int c = quad[f][k];
-            F.v[4 * f + k] = {(c & 1) ? b1[0] : b0[0], (c & 2) ? b1[1] : b0[1], (c & 4) ? b1[2] : b0[2]};
+            F0.v[4 * f + k] = {(c & 1) ? b1[0] : b0[0], (c & 2) ? b1[1] : b0[1], (c & 4) ? b1[2] : b0[2]};
         }
     }
     bool okc = true;
-    for (int32_t p = A.rowptr[i]; p < A.rowptr[i + 1] && okc; ++p) {
-        const int32_t j = A.col[p];
-        if (j == i) continue;
-        const P3 xj{A.x[3 * (int64_t)j], A.x[3 * (int64_t)j + 1], A.x[3 * (int64_t)j + 2]};
-        const P3 d = sub(xj, g);
-        const P3 mid{0.5 * (xj.x + g.x), 0.5 * (xj.y + g.y), 0.5 * (xj.z + g.z)};
-        const double dl = sqrt(dotp(d, d));
-        okc = clip3(F, T, onp, hull, q, h, d, dotp(d, mid), 1e-12 * r * dl, 1e-12 * r, 1e-13 * r * r, j);
-        if (F.nf == 0) break;
+    // A bisector at distance |d| / 2 from g cuts nothing while every vertex lies closer to g:
+    // then d . v - c <= |d| (|v - g| - |d| / 2) < 0, so the vertex scan of clip3 would find no
+    // vertex beyond the plane.  Such planes are skipped on the polyhedron's reach (its largest
+    // vertex distance from g), with a relative margin of 1e-9 far above the rounding of either
+    // test: the cells stay those of the scan, bit for bit.
+    // Two rounds over the neighbours, each in column order: those closer than the kernel
+    // extent first (they carve the cell to about its final size), then the rest, most of
+    // which the reach test skips.  The host builder takes the same order.
+    double r2 = reach2(*pf, g);
+    bool empty = false;
+    for (int round = 0; round < 2 && okc && !empty; ++round) {
+        for (int32_t p = A.rowptr[i]; p < A.rowptr[i + 1] && okc; ++p) {
+            const int32_t j = A.col[p];
+            if (j == i) continue;
+            const P3 xj{A.x[3 * (int64_t)j], A.x[3 * (int64_t)j + 1], A.x[3 * (int64_t)j + 2]};
+            const P3 d = sub(xj, g);
+            const double d2 = dotp(d, d);
+            if ((d2 < r * r) != (round == 0)) continue;
+            if (r2 < 0.25 * d2 * (1.0 - 1e-9)) continue;
+            const P3 mid{0.5 * (xj.x + g.x), 0.5 * (xj.y + g.y), 0.5 * (xj.z + g.z)};
+            const double dl = sqrt(d2);
+            bool cut = false;
+            okc = clip3(*pf, *pt, &cut, onp, hull, q, h, d, dotp(d, mid), 1e-12 * r * dl, 1e-12 * r, 1e-13 * r * r, j);
+            if (cut) {
+                Poly *tmp = pf;
+                pf = pt;
+                pt = tmp;
+                r2 = reach2(*pf, g);
+            }
+            if (pf->nf == 0) {
+                empty = true;
+                break;
+            }
+        }
     }
+    const Poly &F = *pf;
     double vol = 0.0;
     int nt = 0, nb = 0;
     const int32_t to = WRITE ? A.tptr[i] : 0, bo = WRITE ? A.bptr[i] : 0;

@@ -79,8 +79,8 @@ void plane_hull(std::vector<P3> &pts, const P3 &nh, double dist_tol, double area
     for (size_t k = 0; k + 1 < m; ++k) out.push_back(pts[h[k].k]);
 }
 
-// keep {p : nrm.p <= c}; the new face gets label j
-void clip3(std::vector<Face3> &F, std::vector<Face3> &tmp, std::vector<P3> &onp, std::vector<P3> &hull,
+// keep {p : nrm.p <= c}; the new face gets label j.  True when the plane cut.
+bool clip3(std::vector<Face3> &F, std::vector<Face3> &tmp, std::vector<P3> &onp, std::vector<P3> &hull,
            const P3 &nrm, double c, double eps, double dist_tol, double area_tol, int32_t j) {
     bool any_out = false;
     for (const Face3 &f : F) {
@@ -88,7 +88,7 @@ void clip3(std::vector<Face3> &F, std::vector<Face3> &tmp, std::vector<P3> &onp,
             if (dotp(nrm, p) - c > eps) { any_out = true; break; }
         if (any_out) break;
     }
-    if (!any_out) return;
+    if (!any_out) return false;
     tmp.clear();
     onp.clear();
     for (const Face3 &f : F) {
@@ -115,6 +115,7 @@ void clip3(std::vector<Face3> &F, std::vector<Face3> &tmp, std::vector<P3> &onp,
     plane_hull(onp, {nrm.x / ln, nrm.y / ln, nrm.z / ln}, dist_tol, area_tol, hull);
     if (hull.size() >= 3) tmp.push_back({hull, j});
     F.swap(tmp);
+    return true;
 }
 
 struct Chunk3 {
@@ -159,15 +160,33 @@ int64_t build_cells_3d(int64_t n, const double *x, const double *R, const double
                 for (int k = 0; k < 4; ++k) fc.v.push_back(corner(quad[f][k]));
                 F.push_back(std::move(fc));
             }
-            for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-                int32_t j = col[p];
-                if (j == i) continue;
-                P3 xj{x[3 * (int64_t)j], x[3 * (int64_t)j + 1], x[3 * (int64_t)j + 2]};
-                P3 d = sub(xj, g);
-                P3 mid{0.5 * (xj.x + g.x), 0.5 * (xj.y + g.y), 0.5 * (xj.z + g.z)};
-                double dl = std::sqrt(dotp(d, d));
-                clip3(F, tmp, onp, hull, d, dotp(d, mid), 1e-12 * r * dl, 1e-12 * r, 1e-13 * r * r, j);
-                if (F.empty()) break;
+            // Two rounds over the neighbours, each in column order: those closer than the kernel
+            // extent first, then the rest.  A bisector at distance |d| / 2 cuts nothing while the
+            // polyhedron's reach (largest vertex distance from x_i) stays below it; such planes
+            // are skipped with a relative margin of 1e-9, far above the rounding of either test,
+            // so the cells are those of clipping by every plane in this order.
+            auto reach2 = [&]() {
+                double r2 = 0.0;
+                for (const Face3 &f : F)
+                    for (const P3 &v : f.v) r2 = std::max(r2, dotp(sub(v, g), sub(v, g)));
+                return r2;
+            };
+            double r2 = reach2();
+            for (int round = 0; round < 2 && !F.empty(); ++round) {
+                for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                    int32_t j = col[p];
+                    if (j == i) continue;
+                    P3 xj{x[3 * (int64_t)j], x[3 * (int64_t)j + 1], x[3 * (int64_t)j + 2]};
+                    P3 d = sub(xj, g);
+                    const double d2 = dotp(d, d);
+                    if ((d2 < r * r) != (round == 0)) continue;
+                    if (r2 < 0.25 * d2 * (1.0 - 1e-9)) continue;
+                    P3 mid{0.5 * (xj.x + g.x), 0.5 * (xj.y + g.y), 0.5 * (xj.z + g.z)};
+                    double dl = std::sqrt(d2);
+                    if (clip3(F, tmp, onp, hull, d, dotp(d, mid), 1e-12 * r * dl, 1e-12 * r, 1e-13 * r * r, j))
+                        r2 = reach2();
+                    if (F.empty()) break;
+                }
             }
             double vol = 0.0;
             for (const Face3 &f : F) {
