@@ -10,8 +10,11 @@
 // points on edges that lie on the domain boundary.  Chunks of points are
 // evaluated one point per thread (RK moment matrix, Cholesky, corrections and
 // derivatives, FP64), their values written to a shared table, and every thread
-// then accumulates its own (test a, trial b) pairs over the chunk in
-// registers.  The per-cell sums are added into the CSR pattern at the end.
+// then accumulates its own unordered function pairs a <= b over the chunk (the
+// sums of both entries (a, b) and (b, a): the mass, diagonal stiffness and
+// face forms are symmetric, the mixed stiffness forms are each other's
+// transposes, and both gradient forms use the same point values).  The
+// per-cell sums are added into the CSR pattern at the end.
 // Materials are constant over the cell, so sigma-weighted forms are the cell
 // sums times sigma_t(i), sigma_s(i).
 #include <cmath>
@@ -24,8 +27,6 @@ namespace {
 
 constexpr int kMaxS = MLPG_MAX_CELL_FUNCS;
 constexpr int kThreads = 512;
-constexpr int kPairs = kMaxS * kMaxS;
-constexpr int kPPT = (kPairs + kThreads - 1) / kThreads;  // pairs per thread
 constexpr int kChunk = 64;                                       // points per RK chunk
 constexpr int kMaxTri = 64;   // reference triangle rule size cap
 constexpr int kMaxLine = 16;
@@ -359,13 +360,18 @@ struct AsmArgs {
 // CHUNK: quadrature points per RK pass.  The linear path is <1, 40, 64>.
 template <int ORD, int MAXS, int CHUNK>
 __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
-    constexpr int kMaxS = MAXS, kChunk = CHUNK, kPairs = MAXS * MAXS;
+    // unordered pairs a <= b of the staged functions: M0, K^xx, K^yy and the face forms are
+    // symmetric, K^yx(a, b) = K^xy(b, a), and both G(a, b) and G(b, a) come from the same
+    // point values, so one pass over a <= b fills both entries (a, b) and (b, a)
+    constexpr int kMaxS = MAXS, kChunk = CHUNK, kPairs = MAXS * (MAXS + 1) / 2;
     constexpr int kPPT = (kPairs + kThreads - 1) / kThreads;
+    constexpr int kAcc = 11;   // running sums per unordered pair
     static_assert(MAXS <= 64 && CHUNK <= kThreads, "one 64-bit support mask per point");
     const int64_t i = blockIdx.x;
     __shared__ double fx[kMaxS], fy[kMaxS], fR[kMaxS], fV[kMaxS], fR2[kMaxS], finvh[kMaxS];
     __shared__ uint64_t tMask[kChunk];
     __shared__ int32_t fidx[kMaxS];
+    __shared__ uint8_t pairA[kPairs], pairB[kPairs];
     __shared__ int S;
     __shared__ int face_slot[2];
     extern __shared__ double tab[];  // [6][kChunk][kMaxS] + [kChunk] weights + [kChunk] face
@@ -415,14 +421,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
         S = s > kMaxS ? kMaxS : s;
     }
     __syncthreads();
-    const int nS = S;
+    const int nS = S, nP = nS * (nS + 1) / 2;
     const double scale = 0.5 * A.R[i];
-    // pairs owned by this thread: p = tid + k * kThreads, a = p / nS, b = p % nS.
-    // Their nine running sums live in shared memory, sacc[f][p] (one owner per p).
+    // unordered pair p = (a, b), a <= b, row by row of the upper triangle
+    if (tid < nS) {
+        const int a = tid, p0 = a * nS - a * (a - 1) / 2;
+        for (int b = a; b < nS; ++b) {
+            pairA[p0 + b - a] = (uint8_t)a;
+            pairB[p0 + b - a] = (uint8_t)b;
+        }
+    }
+    // pairs owned by this thread: p = tid + k * kThreads.  Their running sums live in
+    // shared memory, sacc[f][p] (one owner per p):
+    //   0 M0, 1-2 G(a, b), 3-4 G(b, a), 5 K^xx, 6 K^xy(a, b), 7 K^yx(a, b), 8 K^yy, 9-10 faces
     double *sacc = tab + 3 * kChunk * kMaxS + kChunk + kChunk / 2 + 1;
     for (int p = tid; p < kPairs; p += kThreads)
 #pragma unroll
-        for (int f = 0; f < 9; ++f) sacc[f * kPairs + p] = 0.0;
+        for (int f = 0; f < kAcc; ++f) sacc[f * kPairs + p] = 0.0;
     double vq0 = 0.0, vqx = 0.0, vqy = 0.0, vb0 = 0.0, vb1 = 0.0;  // vectors for a = tid
 
     // count boundary points of this cell
@@ -484,8 +499,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
 #pragma unroll
             for (int k = 0; k < kPPT; ++k) {
                 int p = tid + k * kThreads;
-                if (p >= nS * nS) break;
-                int a = p / nS, b = p - (p / nS) * nS;
+                if (p >= nP) break;
+                const int a = pairA[p], b = pairB[p];
                 if (!((mk >> a) & (mk >> b) & 1)) continue;   // both functions must be supported here
                 double ua = tU[a * kChunk + qk];
                 double uax = tUx[a * kChunk + qk], uay = tUy[a * kChunk + qk];
@@ -496,12 +511,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
                     sacc[0 * kPairs + p] += wa * ub;
                     sacc[1 * kPairs + p] += wax * ub;
                     sacc[2 * kPairs + p] += way * ub;
-                    sacc[3 * kPairs + p] += wax * ubx;
-                    sacc[4 * kPairs + p] += wax * uby;
-                    sacc[5 * kPairs + p] += way * ubx;
-                    sacc[6 * kPairs + p] += way * uby;
+                    sacc[3 * kPairs + p] += wa * ubx;
+                    sacc[4 * kPairs + p] += wa * uby;
+                    sacc[5 * kPairs + p] += wax * ubx;
+                    sacc[6 * kPairs + p] += wax * uby;
+                    sacc[7 * kPairs + p] += way * ubx;
+                    sacc[8 * kPairs + p] += way * uby;
                 } else {
-                    sacc[(7 + fs) * kPairs + p] += wq * ua * ub;
+                    sacc[(9 + fs) * kPairs + p] += wq * ua * ub;
                 }
             }
             if (tid < nS) {
@@ -519,45 +536,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_assemble_2d(AsmArgs A) {
         }
         __syncthreads();
     }
-    // scatter into the pattern
+    // scatter into the pattern: entry (a, b) and, for a != b, entry (b, a)
     const double st = A.sig_t[i], ss = A.sig_s[i], qi = A.q[i];
     const int64_t nnz = A.nnz, n = A.n;
-#pragma unroll
-    for (int k = 0; k < kPPT; ++k) {
-        int p = tid + k * kThreads;
-        if (p >= nS * nS) break;
-        int a = p / nS, b = p - (p / nS) * nS;
-        double acc[9];
-        bool any = false;
-#pragma unroll
-        for (int f = 0; f < 9; ++f) {
-            acc[f] = sacc[f * kPairs + p];
-            any |= acc[f] != 0.0;
-        }
-        if (!any) continue;
-        int32_t ra = fidx[a], cb = fidx[b];
+    auto put = [&](int32_t ra, int32_t cb, double v, double m0, double gx, double gy, double kxx, double kxy,
+                   double kyx, double kyy, double f0, double f1) {
         int pos = find_col(A.col, A.rowptr[ra], A.rowptr[ra + 1], cb);
-        if (pos < 0) { atomicOr(A.flag, 8); continue; }
-        double vb = fV[b];
-        double m0 = acc[0] * vb;
+        if (pos < 0) {
+            atomicOr(A.flag, 8);
+            return;
+        }
+        m0 *= v;
         atomicAdd(&A.mats[0 * nnz + pos], m0);
         atomicAdd(&A.mats[1 * nnz + pos], st * m0);
         atomicAdd(&A.mats[2 * nnz + pos], ss * m0);
-        double gx = acc[1] * vb, gy = acc[2] * vb;
+        gx *= v;
+        gy *= v;
         atomicAdd(&A.mats[3 * nnz + pos], gx);
         atomicAdd(&A.mats[4 * nnz + pos], gy);
         atomicAdd(&A.mats[5 * nnz + pos], st * gx);
         atomicAdd(&A.mats[6 * nnz + pos], st * gy);
         atomicAdd(&A.mats[7 * nnz + pos], ss * gx);
         atomicAdd(&A.mats[8 * nnz + pos], ss * gy);
-        atomicAdd(&A.mats[9 * nnz + pos], acc[3] * vb);
-        atomicAdd(&A.mats[10 * nnz + pos], acc[4] * vb);
-        atomicAdd(&A.mats[11 * nnz + pos], acc[5] * vb);
-        atomicAdd(&A.mats[12 * nnz + pos], acc[6] * vb);
-        if (face_slot[0] >= 0 && acc[7] != 0.0)
-            atomicAdd(&A.mats[(13 + face_slot[0]) * nnz + pos], acc[7] * vb);
-        if (face_slot[1] >= 0 && acc[8] != 0.0)
-            atomicAdd(&A.mats[(13 + face_slot[1]) * nnz + pos], acc[8] * vb);
+        atomicAdd(&A.mats[9 * nnz + pos], kxx * v);
+        atomicAdd(&A.mats[10 * nnz + pos], kxy * v);
+        atomicAdd(&A.mats[11 * nnz + pos], kyx * v);
+        atomicAdd(&A.mats[12 * nnz + pos], kyy * v);
+        if (face_slot[0] >= 0 && f0 != 0.0) atomicAdd(&A.mats[(13 + face_slot[0]) * nnz + pos], f0 * v);
+        if (face_slot[1] >= 0 && f1 != 0.0) atomicAdd(&A.mats[(13 + face_slot[1]) * nnz + pos], f1 * v);
+    };
+#pragma unroll
+    for (int k = 0; k < kPPT; ++k) {
+        int p = tid + k * kThreads;
+        if (p >= nP) break;
+        const int a = pairA[p], b = pairB[p];
+        double acc[kAcc];
+        bool any = false;
+#pragma unroll
+        for (int f = 0; f < kAcc; ++f) {
+            acc[f] = sacc[f * kPairs + p];
+            any |= acc[f] != 0.0;
+        }
+        if (!any) continue;
+        // (a, b): trial function b carries V_b; (b, a): G from the (b, a) sums, K^xy and K^yx swap
+        put(fidx[a], fidx[b], fV[b], acc[0], acc[1], acc[2], acc[5], acc[6], acc[7], acc[8], acc[9], acc[10]);
+        if (a != b)
+            put(fidx[b], fidx[a], fV[a], acc[0], acc[3], acc[4], acc[5], acc[7], acc[6], acc[8], acc[9], acc[10]);
     }
     if (tid < nS) {
         int32_t a = fidx[tid];
@@ -677,7 +701,8 @@ mlpg_status run_assemble(mlpg_ctx *ctx) {
     a.mats = ctx->mats; a.vecs = ctx->vecs; a.flag = ctx->d_flag;
     // shared table + weights + faces + pair sums for <ORD, MAXS, CHUNK>
     auto run = [&](auto kern, int maxs, int chunk) -> mlpg_status {
-        size_t smem = sizeof(double) * (3 * (size_t)chunk * maxs + chunk + chunk / 2 + 1 + 9 * (size_t)maxs * maxs);
+        size_t smem = sizeof(double) * (3 * (size_t)chunk * maxs + chunk + chunk / 2 + 1 +
+                                        11 * (size_t)maxs * (maxs + 1) / 2);
         CU(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kern<<<ctx->n, kThreads, smem, ctx->stream>>>(a);
         CU_LAUNCH(ctx);

@@ -16,10 +16,32 @@
 //   * for every slot, the pattern entry it holds (perm) and that entry's
 //     column as an index into the halo (lcol).
 #include <algorithm>
+#include <thread>
 
 #include "internal.h"
 
 namespace mlpg {
+
+namespace {
+// threads for the per-tile passes: the host cores, fewer when their n-sized
+// scratch (12 bytes a point each) would pass 256 MB
+int tile_threads(int64_t n, int64_t ntile) {
+    int64_t T = std::max(1u, std::thread::hardware_concurrency());
+    T = std::min<int64_t>(T, std::max<int64_t>(1, (int64_t(256) << 20) / std::max<int64_t>(1, 12 * n)));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(T, ntile / 8));
+}
+template <typename F>
+void over_tiles(int64_t ntile, int T, F &&f) {   // f(first tile, end tile, worker)
+    if (T <= 1) {
+        f(int64_t(0), ntile, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int w = 0; w < T; ++w)
+        th.emplace_back([&, w]() { f(ntile * w / T, ntile * (w + 1) / T, w); });
+    for (auto &x : th) x.join();
+}
+}  // namespace
 
 int64_t build_tiles(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *order, int rows_per_tile,
                     int width_multiple, TileLayout &out) {
@@ -27,46 +49,66 @@ int64_t build_tiles(int64_t n, const int32_t *rowptr, const int32_t *col, const 
     out = TileLayout{};
     out.rows_per_tile = rows_per_tile;
     out.ntile = (n + TR - 1) / TR;
-    out.base.assign(out.ntile + 1, 0);
-    out.width.assign(out.ntile, 0);
-    out.row.assign(out.ntile * TR, -1);
-    out.hptr.assign(out.ntile + 1, 0);
-    // widths, halo sizes and the total slot count
-    std::vector<int32_t> h;
-    for (int64_t t = 0; t < out.ntile; ++t) {
-        int32_t w = 0;
-        h.clear();
-        for (int64_t s = 0; s < TR && t * TR + s < n; ++s) {
-            const int32_t i = order[t * TR + s];
-            out.row[t * TR + s] = i;
-            w = std::max(w, rowptr[i + 1] - rowptr[i]);
-            h.insert(h.end(), col + rowptr[i], col + rowptr[i + 1]);
+    const int64_t ntile = out.ntile;
+    out.base.assign(ntile + 1, 0);
+    out.width.assign(ntile, 0);
+    out.row.assign(ntile * TR, -1);
+    out.hptr.assign(ntile + 1, 0);
+    const int T = tile_threads(n, ntile);
+    // 1. per tile: rows, width and halo.  The halo is collected with a stamp per column
+    //    (stamp[c] == t: already in it), then sorted; linear in the pattern entries.
+    std::vector<std::vector<int32_t>> halo(ntile);
+    over_tiles(ntile, T, [&](int64_t t0, int64_t t1, int) {
+        std::vector<int64_t> stamp(n, -1);
+        for (int64_t t = t0; t < t1; ++t) {
+            int32_t w = 0;
+            std::vector<int32_t> &h = halo[t];
+            for (int64_t s = 0; s < TR && t * TR + s < n; ++s) {
+                const int32_t i = order[t * TR + s];
+                out.row[t * TR + s] = i;
+                w = std::max(w, rowptr[i + 1] - rowptr[i]);
+                for (int32_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+                    if (stamp[col[p]] != t) {
+                        stamp[col[p]] = t;
+                        h.push_back(col[p]);
+                    }
+            }
+            std::sort(h.begin(), h.end());
+            out.width[t] = (w + width_multiple - 1) / width_multiple * width_multiple;
         }
-        std::sort(h.begin(), h.end());
-        h.erase(std::unique(h.begin(), h.end()), h.end());
-        w = (w + width_multiple - 1) / width_multiple * width_multiple;
-        out.width[t] = w;
-        out.base[t + 1] = out.base[t] + (int64_t)w * TR;
-        out.hptr[t + 1] = out.hptr[t] + (int64_t)h.size();
-        out.hcol.insert(out.hcol.end(), h.begin(), h.end());
-        out.max_halo = std::max<int64_t>(out.max_halo, (int64_t)h.size());
-        out.max_width = std::max<int32_t>(out.max_width, w);
+    });
+    for (int64_t t = 0; t < ntile; ++t) {
+        out.base[t + 1] = out.base[t] + (int64_t)out.width[t] * TR;
+        out.hptr[t + 1] = out.hptr[t] + (int64_t)halo[t].size();
+        out.max_halo = std::max<int64_t>(out.max_halo, (int64_t)halo[t].size());
+        out.max_width = std::max<int32_t>(out.max_width, out.width[t]);
     }
-    const int64_t nslot = out.base[out.ntile];
+    out.hcol.resize(out.hptr[ntile]);
+    const int64_t nslot = out.base[ntile];
     out.perm.assign(nslot, -1);
     out.lcol.assign(nslot, 0);
-    for (int64_t t = 0; t < out.ntile; ++t) {
-        const int32_t *hb = out.hcol.data() + out.hptr[t], *he = out.hcol.data() + out.hptr[t + 1];
-        for (int64_t s = 0; s < TR; ++s) {
-            const int32_t i = out.row[t * TR + s];
-            if (i < 0) continue;
-            for (int32_t p = rowptr[i], k = 0; p < rowptr[i + 1]; ++p, ++k) {
-                const int64_t e = out.base[t] + (int64_t)k * TR + s;
-                out.perm[e] = p;
-                out.lcol[e] = (int32_t)(std::lower_bound(hb, he, col[p]) - hb);
+    // 2. per tile: the halo into place and every slot's entry and halo index (pos[c]: the
+    //    column's index in the tile's halo), slots in memory order
+    over_tiles(ntile, T, [&](int64_t t0, int64_t t1, int) {
+        std::vector<int32_t> pos(n, 0);
+        for (int64_t t = t0; t < t1; ++t) {
+            const std::vector<int32_t> &h = halo[t];
+            std::copy(h.begin(), h.end(), out.hcol.begin() + out.hptr[t]);
+            for (int32_t k = 0; k < (int32_t)h.size(); ++k) pos[h[k]] = k;
+            const int32_t *rows = out.row.data() + t * TR;
+            for (int32_t k = 0; k < out.width[t]; ++k) {
+                int32_t *pe = out.perm.data() + out.base[t] + (int64_t)k * TR;
+                int32_t *le = out.lcol.data() + out.base[t] + (int64_t)k * TR;
+                for (int64_t s = 0; s < TR; ++s) {
+                    const int32_t i = rows[s];
+                    if (i < 0 || k >= rowptr[i + 1] - rowptr[i]) continue;
+                    const int32_t p = rowptr[i] + k;
+                    pe[s] = p;
+                    le[s] = pos[col[p]];
+                }
             }
         }
-    }
+    });
     return nslot;
 }
 
