@@ -132,7 +132,9 @@ __device__ bool rk_point(double px, double py, double s, int S, const double *fx
 __device__ uint64_t rk_point_tab(double px, double py, double s, int S, const double *fx, const double *fy,
                                  const double *fR2, const double *finvh, const double *fV, double *U, double *Ux,
                                  double *Uy, int stride) {
-    double M[3][3] = {{0}}, Dx[3][3] = {{0}}, Dy[3][3] = {{0}};
+    // M, Dx, Dy are symmetric: their six distinct entries (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
+    constexpr int EI[6] = {0, 0, 0, 1, 1, 2}, EJ[6] = {0, 1, 2, 1, 2, 2};
+    double m[6] = {0}, mx[6] = {0}, my[6] = {0};
     const double is = 1.0 / s;
     uint64_t mask = 0;
     for (int a = 0; a < S; ++a) {
@@ -154,43 +156,43 @@ __device__ uint64_t rk_point_tab(double px, double py, double s, int S, const do
         Ux[a * stride] = Wx;
         Uy[a * stride] = Wy;
         const double P[3] = {1.0, dx * is, dy * is};
+        const double vW = v * W, vWx = v * Wx, vWy = v * Wy;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                double pp = P[i] * P[j];
-                M[i][j] += v * W * pp;
-                double ex = ((i == 1) * P[j] + (j == 1) * P[i]) * is;
-                double ey = ((i == 2) * P[j] + (j == 2) * P[i]) * is;
-                Dx[i][j] += v * (ex * W + pp * Wx);
-                Dy[i][j] += v * (ey * W + pp * Wy);
-            }
+        for (int e = 0; e < 6; ++e) {
+            const int i = EI[e], j = EJ[e];
+            const double pp = P[i] * P[j];
+            const double ex = ((i == 1) * P[j] + (j == 1) * P[i]) * is;
+            const double ey = ((i == 2) * P[j] + (j == 2) * P[i]) * is;
+            m[e] += vW * pp;
+            mx[e] += ex * vW + pp * vWx;
+            my[e] += ey * vW + pp * vWy;
+        }
     }
-    double L00 = M[0][0];
+    // M = L L^T; the triangular solves multiply by the reciprocal pivots
+    double L00 = m[0];
     if (!(L00 > 0.0)) return 0;
     L00 = sqrt(L00);
-    double L10 = M[1][0] / L00, L20 = M[2][0] / L00;
-    double d1 = M[1][1] - L10 * L10;
-    if (!(d1 > 1e-14 * M[1][1])) return 0;
-    double L11 = sqrt(d1);
-    double L21 = (M[2][1] - L20 * L10) / L11;
-    double d2 = M[2][2] - L20 * L20 - L21 * L21;
-    if (!(d2 > 1e-14 * M[2][2])) return 0;
-    double L22 = sqrt(d2);
+    const double r00 = 1.0 / L00;
+    const double L10 = m[1] * r00, L20 = m[2] * r00;
+    const double d1 = m[3] - L10 * L10;
+    if (!(d1 > 1e-14 * m[3])) return 0;
+    const double L11 = sqrt(d1), r11 = 1.0 / L11;
+    const double L21 = (m[4] - L20 * L10) * r11;
+    const double d2 = m[5] - L20 * L20 - L21 * L21;
+    if (!(d2 > 1e-14 * m[5])) return 0;
+    const double r22 = 1.0 / sqrt(d2);
     auto solve = [&](double b0, double b1, double b2, double *o) {
-        double y0 = b0 / L00, y1 = (b1 - L10 * y0) / L11, y2 = (b2 - L20 * y0 - L21 * y1) / L22;
-        o[2] = y2 / L22;
-        o[1] = (y1 - L21 * o[2]) / L11;
-        o[0] = (y0 - L10 * o[1] - L20 * o[2]) / L00;
+        double y0 = b0 * r00, y1 = (b1 - L10 * y0) * r11, y2 = (b2 - L20 * y0 - L21 * y1) * r22;
+        o[2] = y2 * r22;
+        o[1] = (y1 - L21 * o[2]) * r11;
+        o[0] = (y0 - L10 * o[1] - L20 * o[2]) * r00;
     };
     double C[3], Cx[3], Cy[3];
     solve(1.0, 0.0, 0.0, C);
-    solve(-(Dx[0][0] * C[0] + Dx[0][1] * C[1] + Dx[0][2] * C[2]),
-          -(Dx[1][0] * C[0] + Dx[1][1] * C[1] + Dx[1][2] * C[2]),
-          -(Dx[2][0] * C[0] + Dx[2][1] * C[1] + Dx[2][2] * C[2]), Cx);
-    solve(-(Dy[0][0] * C[0] + Dy[0][1] * C[1] + Dy[0][2] * C[2]),
-          -(Dy[1][0] * C[0] + Dy[1][1] * C[1] + Dy[1][2] * C[2]),
-          -(Dy[2][0] * C[0] + Dy[2][1] * C[1] + Dy[2][2] * C[2]), Cy);
+    solve(-(mx[0] * C[0] + mx[1] * C[1] + mx[2] * C[2]), -(mx[1] * C[0] + mx[3] * C[1] + mx[4] * C[2]),
+          -(mx[2] * C[0] + mx[4] * C[1] + mx[5] * C[2]), Cx);
+    solve(-(my[0] * C[0] + my[1] * C[1] + my[2] * C[2]), -(my[1] * C[0] + my[3] * C[1] + my[4] * C[2]),
+          -(my[2] * C[0] + my[4] * C[1] + my[5] * C[2]), Cy);
     for (uint64_t bits = mask; bits; bits &= bits - 1) {
         const int a = __ffsll((long long)bits) - 1;
         const double W = U[a * stride], Wx = Ux[a * stride], Wy = Uy[a * stride];
