@@ -44,9 +44,11 @@ def _args():
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-pointer end-to-end solves")
-    ap.add_argument("--mode", default="solve", choices=["solve", "apply"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "apply", "apply3d"],
                     help="solve: whole solves (the benchmark); apply: only the batched L-apply of the "
-                         "workload, timed per launch (used for kernel profiles)")
+                         "workload, timed per launch (used for kernel profiles); apply3d: the same for the "
+                         "3D configuration (lognormal sigma, the Alg. 2 set refined within 15 degrees of +x)")
+    ap.add_argument("--side3", type=int, default=40, help="apply3d: points per side (default 40)")
     ap.add_argument("--be-steps", type=int, default=None,
                     help="backward-Euler steps per solve (default: the workload's 20; profiling runs use fewer)")
     ap.add_argument("--no-extras", action="store_true",
@@ -218,9 +220,11 @@ def _reference(args):
     print(json.dumps(line))
 
 
-def _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank):
+def _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank, workload=WORKLOAD):
     """Time the batched L-apply alone on the workload's operators (one launch
-    per step, CUDA events on the library stream); used for kernel profiles."""
+    per step, CUDA events on the library stream); used for kernel profiles.
+    3D: reported against the FP32 FMA peak (ten FMAs per entry and direction),
+    with the HBM figures beside it."""
     import torch
     o = pkg.mlpg_default_options(**opts)
     ctx = pkg.mlpg_create_dev(o, prob.n, prob.m, dv["x"].data_ptr(), dv["R"].data_ptr(), dv["om"].data_ptr(),
@@ -248,16 +252,22 @@ def _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank):
     us = 1e3 * statistics.median(times)
     hbm, kind = _peaks()
     gbs = st["spmm_bytes"] / (us * 1e-6) / 1e9
+    roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "peak_kind": kind,
+            "bytes_per_launch": st["spmm_bytes"]}
+    if prob.dim == 3 and prec == pkg.MLPG_MIXED:
+        tfma = 10.0 * st["nnz"] * prob.m / (us * 1e-6) / 1e12
+        roof = {"bound": "alu", "achieved": tfma, "peak": FP32_FMA_PEAK_T, "unit": "TFMA/s",
+                "frac": tfma / FP32_FMA_PEAK_T, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                "hbm": {"achieved_gbs": gbs, "frac": gbs / hbm, "bytes_per_launch": st["spmm_bytes"]}}
     if rank == 0:
         print(json.dumps({"metric": "batched L-apply", "value": us, "unit": "us/launch", "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
                           "dtype": "f32" if prec == pkg.MLPG_MIXED else "f64",
-                          "config": {"workload": WORKLOAD, "mode": "apply",
+                          "config": {"workload": workload, "mode": args.mode, "points": prob.n,
+                                     "directions": prob.m, "nnz": st["nnz"],
                                      "apply_kernel": st["apply_kernel"], "tile_chunk": st["tile_chunk"],
                                      "options": {k: opts.get(k) for k in ("apply_kernel", "tile_rows", "tile_dpt")}},
-                          "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
-                                       "frac": gbs / hbm, "peak_kind": kind,
-                                       "bytes_per_launch": st["spmm_bytes"]}}))
+                          "roofline": roof}))
 
 
 GOLDEN = os.path.join(ROOT, "tests", "golden", "two_region_256_phi.npz")
@@ -400,7 +410,10 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     # independent problems per rank (weak scaling): seed by rank
-    prob = mi.two_region_2d(n_per_dim=args.n, seed=2000 + rank)
+    if args.mode == "apply3d":
+        prob = mi.lognormal_3d(args.side3, refine=(1, 5, 15.0), seed=3000 + rank)
+    else:
+        prob = mi.two_region_2d(n_per_dim=args.n, seed=2000 + rank)
     if args.be_steps is not None:
         prob.steps = args.be_steps
     prec = pkg.MLPG_MIXED if args.precision == "mixed" else pkg.MLPG_FP64
@@ -409,7 +422,7 @@ def main():
     torch.cuda.set_stream(stream)
     opts = dict(precision=prec, stream=stream.cuda_stream)
     tuned = None
-    if prec == pkg.MLPG_MIXED and not args.no_tune:
+    if prec == pkg.MLPG_MIXED and not args.no_tune and args.mode != "apply3d":   # 3D: the automatic choice
         from paper_2008_02205_gb300 import autotune
         tuned = autotune.tuned_options(prob, stream=stream)   # times each tile shape once, then cached
         opts.update(tuned)
@@ -448,6 +461,10 @@ def main():
 
     if args.mode == "apply":
         _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank)
+        return
+    if args.mode == "apply3d":
+        _apply_mode(args, pkg, prob, prec, opts, dv, stream, world, rank,
+                    workload=f"3d-lognormal-{args.side3}^3-refined{prob.m}")
         return
     for _ in range(args.warmup):
         solve_device()
