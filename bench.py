@@ -420,7 +420,7 @@ def main():
     # a dedicated stream: the library runs on it and the CUDA events below are recorded on it
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    opts = dict(precision=prec, stream=stream.cuda_stream)
+    opts = dict(precision=prec, stream=stream.cuda_stream, dim=prob.dim, lo=tuple(prob.lo), hi=tuple(prob.hi))
     tuned = None
     if prec == pkg.MLPG_MIXED and not args.no_tune and args.mode != "apply3d":   # 3D: the automatic choice
         from paper_2008_02205_gb300 import autotune
