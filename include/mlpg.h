@@ -76,7 +76,7 @@ typedef struct {
                               below outer_tol of Phi (max_outer iterations); default 0 */
     int rk_order;          /* order of the RK correction (Sec. 2.2): 0 (constants reproduced),
                               1 (linear) or 2 (quadratic; needs kernels spanning at least five
-                              neighbours, e.g. extent 2.5-3 point spacings); 3D: 1 only;
+                              neighbours, e.g. extent 2.5-3 point spacings); 3D: 0 or 1;
                               default 1 */
     void *stream;          /* cudaStream_t to run on; NULL = a stream owned by the library */
     int apply_kernel;      /* MLPG_MIXED batched L-apply: 0 = automatic (m % 4 == 0: row tiles with a

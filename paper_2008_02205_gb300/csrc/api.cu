@@ -105,7 +105,7 @@ mlpg_status create_common(const mlpg_options *opt, int64_t n, const double *poin
         (opt->outer_precond != 0 && opt->outer_precond != 1) || (opt->outer_precond == 1 && opt->outer_method != 0) ||
         (opt->outer_precond == 1 && (!(opt->dsa_tol > 0.0) || opt->dsa_max < 1)) ||
         (opt->cells_3d != 0 && opt->cells_3d != 1) ||
-        (opt->dim == 3 && opt->rk_order != 1) || opt->check_every < 1 || !(opt->c > 0) ||
+        (opt->dim == 3 && opt->rk_order > 1) || opt->check_every < 1 || !(opt->c > 0) ||
         !(opt->tau_factor >= 0) || (opt->precision != MLPG_FP64 && opt->precision != MLPG_MIXED))
         return MLPG_ERR_ARG;
     for (int a = 0; a < opt->dim; ++a)

@@ -3,8 +3,9 @@
 // forms).  Each element's quadrature points are mapped from the reference rule
 // (App. A); the functions supported at any of its points are taken from the
 // overlap row of the cell's generator; the RK functions and gradients are
-// evaluated warp-cooperatively per point (Sec. 2.2, basis P = [1, (x - x_j)/s],
-// s = h of the generator); every pair's forms are summed over the element's
+// evaluated warp-cooperatively per point (Sec. 2.2, basis P = [1, (x - x_j)/s]
+// for the linear correction or P = [1] for order 0, s = h of the generator);
+// every pair's forms are summed over the element's
 // points in registers and added to the shared pattern with FP64 atomics.
 //
 // mats layout in 3D: 0 M0, 1 Mt, 2 Ms, 3-5 G, 6-8 Gt, 9-11 Gs, 12-20 K (a-major),
@@ -43,22 +44,27 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// index of the symmetric 4x4 entry (i <= j) in a packed array of 10
-__device__ __forceinline__ int sym4(int i, int j) {
-    return i <= j ? i * 4 - i * (i - 1) / 2 + (j - i) : j * 4 - j * (j - 1) / 2 + (i - j);
+// index of the symmetric NP x NP entry (i, j) in a packed array of NP (NP + 1) / 2
+template <int NP>
+__device__ __forceinline__ int symn(int i, int j) {
+    return i <= j ? i * NP - i * (i - 1) / 2 + (j - i) : j * NP - j * (j - 1) / 2 + (i - j);
 }
 
 // RK functions of the S staged functions at p (one warp; lane owns a = lane +
-// 32 k).  Writes U, dU (3 components) at tab[c * cs + a], c = 0..3, and the
+// 32 k), basis P_j = [1] (order 0, NP = 1) or [1, (p - x_j)/s] (order 1,
+// NP = 4).  Writes U, dU (3 components) at tab[c * cs + a], c = 0..3, and the
 // support mask bits into mk[2].  Returns false when the moment matrix is not
 // positive definite.
+template <int NP>
 __device__ bool rk3_warp(const double p[3], double s, int S, const double *fx, const double *fR2,
                          const double *finvh, const double *fV, double *tab, int cs, uint64_t *mk) {
+    static_assert(NP == 1 || NP == 4, "order 0 or 1");
+    constexpr int NE = NP * (NP + 1) / 2;
     const int lane = threadIdx.x & 31;
     const double is = 1.0 / s;
-    double M[10], D[3][10];
+    double M[NE], D[3][NE];
 #pragma unroll
-    for (int e = 0; e < 10; ++e) { M[e] = 0.0; D[0][e] = D[1][e] = D[2][e] = 0.0; }
+    for (int e = 0; e < NE; ++e) { M[e] = 0.0; D[0][e] = D[1][e] = D[2][e] = 0.0; }
     double Wl[3], Gl[3][3];
     bool on[3];
 #pragma unroll
@@ -78,23 +84,23 @@ __device__ bool rk3_warp(const double p[3], double s, int S, const double *fx, c
         const double Wg[3] = {g * d0, g * d1, g * d2}, v = fV[a];
         Wl[k] = W;
         Gl[k][0] = Wg[0]; Gl[k][1] = Wg[1]; Gl[k][2] = Wg[2];
-        const double P[4] = {1.0, d0 * is, d1 * is, d2 * is};
+        const double Pall[4] = {1.0, d0 * is, d1 * is, d2 * is};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < NP; ++i)
 #pragma unroll
-            for (int j = i; j < 4; ++j) {
-                const int e = sym4(i, j);
-                const double pp = P[i] * P[j];
+            for (int j = i; j < NP; ++j) {
+                const int e = symn<NP>(i, j);
+                const double pp = Pall[i] * Pall[j];
                 M[e] += v * W * pp;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const double dp = ((i == c + 1) * P[j] + (j == c + 1) * P[i]) * is;
+                    const double dp = ((i == c + 1) * Pall[j] + (j == c + 1) * Pall[i]) * is;
                     D[c][e] += v * (dp * W + pp * Wg[c]);
                 }
             }
     }
 #pragma unroll
-    for (int e = 0; e < 10; ++e) {
+    for (int e = 0; e < NE; ++e) {
         M[e] = warp_sum(M[e]);
         D[0][e] = warp_sum(D[0][e]);
         D[1][e] = warp_sum(D[1][e]);
@@ -111,76 +117,87 @@ __device__ bool rk3_warp(const double p[3], double s, int S, const double *fx, c
         }
     }
     // Cholesky of M (every lane, same values)
-    double L[4][4];
+    double L[NP][NP];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < NP; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) L[i][j] = 0.0;
+        for (int j = 0; j < NP; ++j) L[i][j] = 0.0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        double dsum = M[sym4(j, j)];
+    for (int j = 0; j < NP; ++j) {
+        double dsum = M[symn<NP>(j, j)];
 #pragma unroll
         for (int k = 0; k < j; ++k) dsum -= L[j][k] * L[j][k];
-        if (!(dsum > 1e-14 * M[sym4(j, j)])) return false;
+        if (!(dsum > 1e-14 * M[symn<NP>(j, j)])) return false;
         L[j][j] = sqrt(dsum);
 #pragma unroll
-        for (int i = j + 1; i < 4; ++i) {
-            double t = M[sym4(i, j)];
+        for (int i = j + 1; i < NP; ++i) {
+            double t = M[symn<NP>(i, j)];
 #pragma unroll
             for (int k = 0; k < j; ++k) t -= L[i][k] * L[j][k];
             L[i][j] = t / L[j][j];
         }
     }
-    auto solve = [&](const double b[4], double o[4]) {
-        double y[4];
+    auto solve = [&](const double b[NP], double o[NP]) {
+        double y[NP];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < NP; ++i) {
             double t = b[i];
 #pragma unroll
             for (int k = 0; k < i; ++k) t -= L[i][k] * y[k];
             y[i] = t / L[i][i];
         }
 #pragma unroll
-        for (int i = 3; i >= 0; --i) {
+        for (int i = NP - 1; i >= 0; --i) {
             double t = y[i];
 #pragma unroll
-            for (int k = i + 1; k < 4; ++k) t -= L[k][i] * o[k];
+            for (int k = i + 1; k < NP; ++k) t -= L[k][i] * o[k];
             o[i] = t / L[i][i];
         }
     };
-    double C[4], Cd[3][4];
-    const double e1[4] = {1.0, 0.0, 0.0, 0.0};
+    // C = M^-1 e1, and its derivatives Cd[c] = -M^-1 (dM/dx_c) C
+    double C[NP], Cd[3][NP];
+    double e1[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) e1[i] = i == 0 ? 1.0 : 0.0;
     solve(e1, C);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        double b[4];
+        double b[NP];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < NP; ++i) {
             double t = 0.0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) t += D[c][sym4(i, j)] * C[j];
+            for (int j = 0; j < NP; ++j) t += D[c][symn<NP>(i, j)] * C[j];
             b[i] = -t;
         }
         solve(b, Cd[c]);
     }
+    // U_a = W_a P_a . C;  d_c U_a = W_a (dP_a/dx_c . C + P_a . Cd[c]) + (P_a . C) dW_a/dx_c
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int a = lane + 32 * k;
         if (a >= S) continue;
-        double u = 0.0, ux = 0.0, uy = 0.0, uz = 0.0;
+        double u = 0.0, ud[3] = {0.0, 0.0, 0.0};
         if (on[k]) {
-            const double P1 = (p[0] - fx[3 * a]) * is, P2 = (p[1] - fx[3 * a + 1]) * is, P3 = (p[2] - fx[3 * a + 2]) * is;
-            const double PC = C[0] + P1 * C[1] + P2 * C[2] + P3 * C[3];
+            const double Pall[4] = {1.0, (p[0] - fx[3 * a]) * is, (p[1] - fx[3 * a + 1]) * is,
+                                    (p[2] - fx[3 * a + 2]) * is};
+            double PC = 0.0;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) PC += Pall[i] * C[i];
             const double W = Wl[k];
             u = W * PC;
-            ux = W * (C[1] * is + Cd[0][0] + P1 * Cd[0][1] + P2 * Cd[0][2] + P3 * Cd[0][3]) + PC * Gl[k][0];
-            uy = W * (C[2] * is + Cd[1][0] + P1 * Cd[1][1] + P2 * Cd[1][2] + P3 * Cd[1][3]) + PC * Gl[k][1];
-            uz = W * (C[3] * is + Cd[2][0] + P1 * Cd[2][1] + P2 * Cd[2][2] + P3 * Cd[2][3]) + PC * Gl[k][2];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double t = NP > 1 ? C[NP > 1 ? c + 1 : 0] * is : 0.0;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) t += Pall[i] * Cd[c][i];
+                ud[c] = W * t + PC * Gl[k][c];
+            }
         }
         tab[a] = u;
-        tab[cs + a] = ux;
-        tab[2 * cs + a] = uy;
-        tab[3 * cs + a] = uz;
+        tab[cs + a] = ud[0];
+        tab[2 * cs + a] = ud[1];
+        tab[3 * cs + a] = ud[2];
     }
     return true;
 }
@@ -209,7 +226,7 @@ struct Asm3Args {
 
 // BND = false: tetrahedra (generator, v0, v1, v2) -> M0, Mt, Ms, G, Gt, Gs, K, Q0, Q.
 // BND = true: boundary triangles (v0, v1, v2) on face f -> S_f, B_f.
-template <bool BND>
+template <bool BND, int NP>
 __global__ void __launch_bounds__(kThreads3) k_assemble_3d(Asm3Args A) {
     __shared__ double fx[3 * kMaxS3], fR2[kMaxS3], finvh[kMaxS3], fV[kMaxS3];
     __shared__ int32_t fidx[kMaxS3];
@@ -310,7 +327,7 @@ __global__ void __launch_bounds__(kThreads3) k_assemble_3d(Asm3Args A) {
     const double s = 0.5 * A.R[o];
     for (int q = warp; q < nq; q += kThreads3 / 32) {
         const double p[3] = {qx[3 * q], qx[3 * q + 1], qx[3 * q + 2]};
-        if (!rk3_warp(p, s, S, fx, fR2, finvh, fV, tab + (int64_t)q * 4 * kMaxS3, kMaxS3, qmk[q])) {
+        if (!rk3_warp<NP>(p, s, S, fx, fR2, finvh, fV, tab + (int64_t)q * 4 * kMaxS3, kMaxS3, qmk[q])) {
             if (lane == 0) atomicOr(A.flag, 1);
         }
     }
@@ -393,6 +410,7 @@ __global__ void __launch_bounds__(kThreads3) k_assemble_3d(Asm3Args A) {
 }
 
 // interp[pos(i, j)] = V_j U_j(x_i): one warp per point, candidates from row i
+template <int NP>
 __global__ void __launch_bounds__(128) k_interp_3d(int64_t n, const double *__restrict__ x,
                                                    const double *__restrict__ R, const double *__restrict__ V,
                                                    const int32_t *__restrict__ rowptr,
@@ -436,7 +454,7 @@ __global__ void __launch_bounds__(128) k_interp_3d(int64_t n, const double *__re
         return;
     }
     __syncwarp();
-    if (!rk3_warp(p, 0.5 * R[i], S, fx[w], fR2[w], finvh[w], fV[w], tab[w], kMaxS3, mk[w])) {
+    if (!rk3_warp<NP>(p, 0.5 * R[i], S, fx[w], fR2[w], finvh[w], fV[w], tab[w], kMaxS3, mk[w])) {
         if (lane == 0) atomicOr(flag, 1);
         return;
     }
@@ -462,8 +480,12 @@ mlpg_status run_interp_3d(mlpg_ctx *ctx) {
     CU(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
     CU(ctx, cudaMemsetAsync(ctx->interp, 0, ctx->nnz * sizeof(double), ctx->stream));
     const int64_t blocks = (ctx->n + 3) / 4;
-    k_interp_3d<<<(unsigned)blocks, 128, 0, ctx->stream>>>(ctx->n, ctx->x, ctx->R, ctx->V, ctx->rowptr, ctx->col,
-                                                          ctx->interp, ctx->d_flag);
+    if (ctx->opt.rk_order == 0)
+        k_interp_3d<1><<<(unsigned)blocks, 128, 0, ctx->stream>>>(ctx->n, ctx->x, ctx->R, ctx->V, ctx->rowptr,
+                                                                  ctx->col, ctx->interp, ctx->d_flag);
+    else
+        k_interp_3d<4><<<(unsigned)blocks, 128, 0, ctx->stream>>>(ctx->n, ctx->x, ctx->R, ctx->V, ctx->rowptr,
+                                                                  ctx->col, ctx->interp, ctx->d_flag);
     CU_LAUNCH(ctx);
     return check_flag3(ctx, "interpolation");
 }
@@ -499,14 +521,16 @@ mlpg_status run_assemble_3d(mlpg_ctx *ctx) {
     a.nelem = ctx->ntet; a.owner = ctx->tet_owner; a.face = nullptr; a.ev = ctx->tet_v; a.nq = n1 * n1 * n1;
     size_t smem = sizeof(double) * (size_t)a.nq * 4 * kMaxS3;
     if (a.nelem > 0) {
-        k_assemble_3d<false><<<(unsigned)a.nelem, kThreads3, smem, ctx->stream>>>(a);
+        if (ctx->opt.rk_order == 0) k_assemble_3d<false, 1><<<(unsigned)a.nelem, kThreads3, smem, ctx->stream>>>(a);
+        else k_assemble_3d<false, 4><<<(unsigned)a.nelem, kThreads3, smem, ctx->stream>>>(a);
         CU_LAUNCH(ctx);
     }
     // boundary elements
     a.nelem = ctx->nbtri; a.owner = ctx->tri_owner; a.face = ctx->tri_face; a.ev = ctx->tri_v; a.nq = n1 * n1;
     smem = sizeof(double) * (size_t)a.nq * 4 * kMaxS3;
     if (a.nelem > 0) {
-        k_assemble_3d<true><<<(unsigned)a.nelem, kThreads3, smem, ctx->stream>>>(a);
+        if (ctx->opt.rk_order == 0) k_assemble_3d<true, 1><<<(unsigned)a.nelem, kThreads3, smem, ctx->stream>>>(a);
+        else k_assemble_3d<true, 4><<<(unsigned)a.nelem, kThreads3, smem, ctx->stream>>>(a);
         CU_LAUNCH(ctx);
     }
     return check_flag3(ctx, "assembly");

@@ -244,3 +244,36 @@ def test_refined_run_3d_10_cubed_matches_oracle():
         tp.integrate().assemble()
         phi = tp.run(prob.dt, prob.steps)
         assert _rel(phi, ref) < 1e-8
+
+
+def test_rk_order_0_in_3d_forms_and_run():
+    """Order-0 RK functions in 3D (Sec. 2.2: the basis P = [1], Shepard
+    functions that reproduce constants): every integrated form to 1e-12 of
+    its array's magnitude, and a 3-step run in FP64 and mixed precision against
+    the oracle at the same order."""
+    prob = _problem(6, seed=3006)
+    disc = O.Discretization(prob.x, prob.R, prob.lo, prob.hi, rk_order=0)
+    F = disc.assemble_per_point(prob.sigma_t, prob.sigma_s, prob.q)
+    d = 3
+    ref_m = np.concatenate([F["M0"][None], F["Mt"][None], F["Ms"][None], F["G"], F["Gt"], F["Gs"],
+                            F["K"].reshape(d * d, -1), F["S"]])
+    ref_v = np.concatenate([F["Q0"][None], F["Q"], F["B"]])
+    tr = O.Transport(disc, F, prob.omega, prob.w, psi_b=prob.inflow)
+    _, Phi, _ = O.Solver(tr, outer_tol=1e-13).run(np.zeros((tr.M, disc.n)), prob.dt, prob.steps)
+    ref = disc.interpolation_matrix() @ Phi
+    with pkg.TransportProblem.from_problem(prob, rk_order=0, inner_tol=1e-13, outer_tol=1e-13) as tp:
+        tp.integrate().assemble()
+        mats, vecs = tp.forms()
+        for k in range(ref_m.shape[0]):
+            assert np.abs(mats[k] - ref_m[k]).max() <= 1e-12 * np.abs(ref_m[k]).max(), k
+        for k in range(ref_v.shape[0]):
+            assert np.abs(vecs[k] - ref_v[k]).max() <= 1e-12 * max(np.abs(ref_v[k]).max(), 1e-300), k
+        # constants reproduced: sum_j V_j U_j = 1, so V^T M0 1 is the cube's volume
+        rowptr, col = tp.neighbors()
+        import scipy.sparse as sp
+        M0 = sp.csr_matrix((mats[0], col, rowptr), shape=(prob.n, prob.n))
+        assert abs(tp.volumes() @ M0 @ np.ones(prob.n) - 1.0) < 1e-12
+        assert _rel(tp.run(prob.dt, prob.steps), ref) < 1e-9
+    with pkg.TransportProblem.from_problem(prob, rk_order=0, precision=pkg.MLPG_MIXED, refine_tol=1e-12) as tp:
+        tp.integrate().assemble()
+        assert _rel(tp.run(prob.dt, prob.steps), ref) < 1e-8

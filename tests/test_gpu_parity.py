@@ -342,7 +342,9 @@ def test_rk_orders_forms_and_run(order, support):
         assert _rel(tp.run(prob.dt, prob.steps), ref) < 1e-8
 
 
-def test_rk_order_must_be_linear_in_3d():
+def test_rk_order_2_is_refused_in_3d():
+    """3D takes orders 0 and 1; order 2 needs a degree-5 tetrahedron rule and a
+    stronger inner preconditioner than point blocks (not built)."""
     prob = mi.lognormal_3d(4, sn=4, steps=1)
     with pytest.raises(pkg.MlpgError):
         pkg.TransportProblem.from_problem(prob, rk_order=2)
