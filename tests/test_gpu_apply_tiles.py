@@ -144,7 +144,8 @@ GATHER_CASES = [
     # (dim, points per side, S_N or refined set, rows per tile, directions per thread, expected chunk)
     (2, 13, 4, 8, 4, 12),      # m = 12, 169 points: 22 tiles of 8 rows, the last ragged
     (2, 30, 8, 32, 8, 40),     # the benchmark's angular set
-    (2, 17, 12, 32, 4, 44),    # m = 84: two chunks of 44 and 40 (the last chunk's spare lanes read nothing)
+    (2, 17, 12, 16, 4, 44),    # m = 84: two chunks of 44 and 40 (the last chunk's spare lanes read nothing)
+    (2, 17, 12, 32, 4, 28),    # m = 84 on 32-row tiles: three chunks (at most 320 threads per CTA)
     (3, 6, 4, 16, 8, 24),      # 3D, m = 24
     (3, 7, 8, 8, 8, 80),       # 3D, m = 80 in one chunk (the staged-halo tiles need several)
     (3, 7, 8, 4, 4, 80),       # 3D, 4-row tiles
