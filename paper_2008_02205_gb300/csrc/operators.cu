@@ -559,8 +559,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // completing on an mbarrier:
 //   * the halo rows of X (the union of the tile's columns, the chunk's
 //     directions): one copy per row, all on one barrier;
-//   * the tile's record slots, kRecK entries per stage, kRecStages stages in
-//     flight; a stage's buffer is refilled once every thread is done with it.
+//   * the tile's record slots, kRecK entries per stage (kRecKGather in gather
+//     mode), kRecStages stages in flight; a stage's buffer is refilled once every
+//     thread is done with it (a proxy fence and the CTA barrier order the reads
+//     before the refill).
 // Thread (s, g) owns row slot s and DPT directions of the chunk (quads g and
 // g + G, G = mc / DPT, so the threads of a row read one contiguous run of the
 // staged row), combines the K base-array values of an entry with its
