@@ -102,7 +102,9 @@ def _morton(x):
     return np.argsort(code, kind="stable").astype(np.int32)
 
 
-@pytest.mark.parametrize("dim,side,tr", [(2, 13, 64), (2, 30, 64), (2, 30, 16), (3, 7, 64), (3, 6, 8)])
+# the larger cases have enough tiles to run the builder on several host threads
+@pytest.mark.parametrize("dim,side,tr", [(2, 13, 64), (2, 30, 64), (2, 30, 16), (3, 7, 64), (3, 6, 8),
+                                         (2, 48, 8), (3, 9, 4)])
 def test_tiles_cover_the_pattern_once(harness, dim, side, tr):
     x, h = mi.jittered_lattice(side, dim, 77 + side)
     R = np.full(len(x), 2.0 * h)
