@@ -2,6 +2,7 @@
 // host cores (the 2D cells are built on the device, cells2d.cu).
 #include <algorithm>
 #include <cmath>
+#include <exception>
 #include <thread>
 
 #include "internal.h"
@@ -219,10 +220,22 @@ int64_t build_cells_3d(int64_t n, const double *x, const double *R, const double
             if (!(vol > 0.0) && ch.bad < 0) ch.bad = i;
         }
     };
+    // an exception in any share (a failed allocation) is rethrown on this thread once every
+    // worker has ended
+    std::vector<std::exception_ptr> errs(nt);
+    auto guarded = [&](unsigned t) {
+        try {
+            work(t);
+        } catch (...) {
+            errs[t] = std::current_exception();
+        }
+    };
     std::vector<std::thread> th;
-    for (unsigned t = 1; t < nt; ++t) th.emplace_back(work, t);
-    work(0);
+    for (unsigned t = 1; t < nt; ++t) th.emplace_back(guarded, t);
+    guarded(0);
     for (auto &t : th) t.join();
+    for (auto &e : errs)
+        if (e) std::rethrow_exception(e);
     out.tet_owner.clear(); out.tet_v.clear();
     out.tri_owner.clear(); out.tri_face.clear(); out.tri_v.clear();
     for (auto &ch : chunks) {

@@ -16,6 +16,7 @@
 //   * for every slot, the pattern entry it holds (perm) and that entry's
 //     column as an index into the halo (lcol).
 #include <algorithm>
+#include <exception>
 #include <thread>
 
 #include "internal.h"
@@ -30,16 +31,27 @@ int tile_threads(int64_t n, int64_t ntile) {
     T = std::min<int64_t>(T, std::max<int64_t>(1, (int64_t(256) << 20) / std::max<int64_t>(1, 12 * n)));
     return (int)std::max<int64_t>(1, std::min<int64_t>(T, ntile / 8));
 }
+// f(first tile, end tile, worker) over T workers; an exception thrown by a worker (an
+// allocation that fails) is rethrown here, on the calling thread, after every worker ended
 template <typename F>
-void over_tiles(int64_t ntile, int T, F &&f) {   // f(first tile, end tile, worker)
+void over_tiles(int64_t ntile, int T, F &&f) {
     if (T <= 1) {
         f(int64_t(0), ntile, 0);
         return;
     }
+    std::vector<std::exception_ptr> errs(T);
     std::vector<std::thread> th;
     for (int w = 0; w < T; ++w)
-        th.emplace_back([&, w]() { f(ntile * w / T, ntile * (w + 1) / T, w); });
+        th.emplace_back([&, w]() {
+            try {
+                f(ntile * w / T, ntile * (w + 1) / T, w);
+            } catch (...) {
+                errs[w] = std::current_exception();
+            }
+        });
     for (auto &x : th) x.join();
+    for (auto &e : errs)
+        if (e) std::rethrow_exception(e);
 }
 }  // namespace
 
