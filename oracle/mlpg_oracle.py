@@ -29,9 +29,13 @@ diffusion acceleration as future work), or source iteration replaces it.
 ``step_direct`` solves the coupled step system
 (L - MS D) Psi = T Psi^{n-1} + r with one sparse LU and pins the nested scheme.
 
-Unpinned parts: individual off-diagonal values of the SUPG forms have no
-closed form; they are pinned only as a whole through the identities and the
-manufactured-solution convergence orders in tests/test_oracle_*.py.
+Individual values of the SUPG forms have no closed form.  Besides the
+identities and the manufactured-solution convergence orders in
+tests/test_oracle_*.py, single 2D entries (mass, gradient and stiffness forms;
+interior and corner, diagonal and off-diagonal) are checked against an
+independent numpy evaluation of the RK functions, integrated by a converged
+composite Gauss rule, to the rules' quadrature error
+(tests/test_oracle_form_entries.py).
 """
 from __future__ import annotations
 
